@@ -1,0 +1,113 @@
+"""Monodomain time stepping: ionic models (Section 2.3) and the linearly
+implicit step of Section 3.1 with ionic current interpolation.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Per step (Section 3.1, the three bullet points after Eq. fully_discrete):
+  1. ionic ODE at every DoF: w^{n+1} = w^n + dt H(u^n, w^n)
+  2. ionic current at the DoFs, interpolated (ICI): the load is M f with
+     f_i = I_app,i(t_{n+1}) - chi I_ion(U*_i, w_i^{n+1})
+  3. solve A0 u^{n+1} = b by MG-PCG warm-started from u^n.
+
+Scheme: IMEX backward Euler (the workloads' form of Eq. fully_discrete with
+the BDF2 history replaced by one level): mass coefficient c = chi C_m / dt of
+A0 = c M + A, U* = u^n, b = M (c u^n + f). The paper's BDF2 with the
+extrapolation U* = 2u^n - u^{n-1} is not part of this oracle.
+
+Readings: the ionic ODE uses forward Euler (the workloads' "explicit
+update"; the paper integrates it with BDF2). FitzHugh-Nagumo follows
+Section 2.3.1 with k = 1, Gamma = b. Aliev-Panfilov is not in the paper; its
+published form (Aliev & Panfilov 1996) is used:
+  I_ion = k u (u - a)(u - 1) + u w,
+  H     = (eps + mu1 w / (u + mu2)) (-w - k u (u - a - 1)).
+Parity of these constants is unpinned by the paper (chosen readings); the
+pins are the model equilibria and the space-clamped recurrence.
+"""
+from dataclasses import dataclass
+
+import numpy as np
+
+from .multigrid import pcg, vcycle
+
+FHN, ALIEV_PANFILOV = 0, 1
+
+
+def ionic(prm, u, w):
+    """(I_ion(u, w), H(u, w)) of the model in prm (dict as in workloads)."""
+    k, a, eps = prm["k"], prm["a"], prm["eps"]
+    if prm["model"] == FHN:
+        I = k * u * (u - a) * (u - 1.0) + w
+        H = eps * (u - prm["gamma"] * w)
+    else:
+        mu1, mu2 = prm["mu1"], prm["mu2"]
+        I = k * u * (u - a) * (u - 1.0) + u * w
+        H = (eps + mu1 * w / (u + mu2)) * (-w - k * u * (u - a - 1.0))
+    return I, H
+
+
+def ionic_jacobian(prm, u, w):
+    """Partial derivatives (I_u, I_w, H_u, H_w) of the model, pointwise."""
+    k, a, eps = prm["k"], prm["a"], prm["eps"]
+    dI_du = k * (3.0 * u * u - 2.0 * (a + 1.0) * u + a)
+    if prm["model"] == FHN:
+        g = prm["gamma"]
+        return dI_du + 0.0 * w, np.ones_like(w), eps * np.ones_like(u), -eps * g * np.ones_like(w)
+    mu1, mu2 = prm["mu1"], prm["mu2"]
+    I_u = dI_du + w
+    I_w = u.copy()
+    e = eps + mu1 * w / (u + mu2)
+    g = -w - k * u * (u - a - 1.0)
+    e_u = -mu1 * w / (u + mu2) ** 2
+    e_w = mu1 / (u + mu2)
+    g_u = -k * (2.0 * u - a - 1.0)
+    g_w = -1.0
+    return I_u, I_w, e_u * g + e * g_u, e_w * g + e * g_w
+
+
+@dataclass
+class StepOptions:
+    dt: float
+    ionic: dict
+    rtol: float = 1e-8
+    max_it: int = 500
+    chi: float = 1.0
+    cm: float = 1.0
+    iapp_value: float = 1.0
+    iapp_steps: int = 5
+
+    def mass_coeff(self):
+        return self.chi * self.cm / self.dt
+
+
+def iapp(opts: StepOptions, mask, n):
+    """Nodal applied current at t_{n+1}: iapp_value on the stimulated DoFs for
+    the first iapp_steps steps (n = 0 .. iapp_steps-1), zero afterwards."""
+    return opts.iapp_value * mask if n < opts.iapp_steps else np.zeros_like(mask)
+
+
+def rhs(disc, opts: StepOptions, u, w_new, mask, n):
+    """Load vector b of step n -> n+1 (ionic current interpolation: nodal f
+    multiplied by the mass matrix)."""
+    I, _ = ionic(opts.ionic, u, w_new)
+    f = iapp(opts, mask, n) - opts.chi * I
+    return disc.M @ (opts.mass_coeff() * u + f)
+
+
+def step(disc, hier, opts: StepOptions, u, w, mask, n):
+    """One time step n -> n+1. Returns (u_new, w_new, PCGResult)."""
+    _, H = ionic(opts.ionic, u, w)
+    w_new = w + opts.dt * H
+    b = rhs(disc, opts, u, w_new, mask, n)
+    A0 = hier.levels[0].A
+    res = pcg(A0, b, u, lambda r: vcycle(hier, r), opts.rtol, opts.max_it)
+    return res.x, w_new, res
+
+
+def run(disc, hier, opts: StepOptions, u0, w0, mask, n_steps):
+    """n_steps time steps from (u0, w0); returns (u, w, iterations list)."""
+    u, w = u0.copy(), w0.copy()
+    its = []
+    for n in range(n_steps):
+        u, w, res = step(disc, hier, opts, u, w, mask, n)
+        its.append(res.iterations)
+    return u, w, its
