@@ -1,0 +1,335 @@
+"""Benchmark: time steps of the SIPG-DG monodomain model solved by
+agglomerated-multigrid PCG on one GB300 (or N replicas under torchrun).
+
+A "step" is one time step of the hot path: ionic update + right-hand side
+(ionic current interpolation) + PCG to 1e-8 relative residual preconditioned
+by one V-cycle per iteration. Workload: 512x512 jittered quads, DG Q2
+(2,359,296 DoFs), 30-degree fibres, 4 agglomerated levels, FitzHugh-Nagumo,
+dt = 0.05. Every vector and matrix is resident in HBM; the fine matrix
+(0.85 GB float64) is far larger than L2, so every step streams from HBM.
+
+  python bench.py [--steps K] [--warmup W] [--form f32|f64|bf16s] [--impl reference]
+
+Prints one JSON line (rank 0).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time-steps/s and MDoF/s of MG-PCG at 1e-8 rel. residual; % of HBM peak"
+UNIT = "time-steps/s"
+KERNEL_NAMES = {0: "k_spmv<double> (fine float64 SpMV, outer CG)",
+                1: "k_cheb (fine Chebyshev block-Jacobi step, V-cycle precision)"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="f32", choices=["f32", "f64", "bf16s"])
+    ap.add_argument("--n", type=int, default=512, help="elements per direction")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=8)
+    return ap.parse_args()
+
+
+def workload(n):
+    from paper_2602_16312_gb300 import workloads as W
+    return W.jittered_square_2d(n=n, degree=2, n_levels=4)
+
+
+def workload_name(wl):
+    return (f"{wl.name}: {wl.mesh.n_elements} quads, DG Q{wl.degree}, {wl.n_dofs} DoFs, "
+            f"{wl.n_levels} levels (<=16 per agglomerate), FHN, dt {wl.dt}, rtol {wl.rtol}")
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from paper_2602_16312_gb300 import workloads as W
+from oracle import sipg, multigrid as mg, monodomain as md
+wl = W.jittered_square_2d(n={n}, degree=2, n_levels=4)
+disc = sipg.assemble(wl.mesh.vertices, wl.mesh.elements, wl.conductivity, wl.degree, wl.penalty_mode,
+                     wl.penalty_coeff)
+opts = md.StepOptions(dt=wl.dt, ionic=wl.ionic, rtol=wl.rtol, iapp_value=wl.iapp_value, iapp_steps=wl.iapp_steps)
+h = mg.build_hierarchy(disc, opts.mass_coeff(), wl.maps)
+u = np.zeros(disc.n); w = np.zeros(disc.n); mask = wl.stim_mask_nodal()
+t0 = time.perf_counter()
+_, H = md.ionic(wl.ionic, u, w)
+w1 = w + wl.dt * H
+b = md.rhs(disc, opts, u, w1, mask, 0)
+t_rhs = time.perf_counter() - t0
+t0 = time.perf_counter()
+res = mg.pcg(h.levels[0].A, b, u, lambda r: mg.vcycle(h, r), rtol=1e-300, max_it={iters})
+t_it = (time.perf_counter() - t0) / res.iterations
+print(json.dumps(dict(t_rhs=t_rhs, t_iter=t_it, iters=res.iterations)))
+"""
+
+
+def cpu_oracle_sample(n, iters):
+    """Runs the oracle single-threaded in a fresh process (spawned before any
+    GPU work in this process matters): ionic + RHS of step 0 and `iters` PCG
+    iterations of its solve, timed on this host's cores."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", ORACLE_SNIPPET.format(root=ROOT, n=n, iters=iters)],
+                         env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError("oracle leg failed: " + out.stderr.decode()[-2000:])
+    return json.loads(out.stdout.decode().strip().splitlines()[-1])
+
+
+def cpu_baseline_entry(sample, iters_per_step, n):
+    t_step = sample["t_rhs"] + sample["t_iter"] * iters_per_step
+    return {"value": 1.0 / t_step, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"oracle (numpy/scipy float64, 1 thread) on the {n}x{n} Q2 workload: ionic+RHS of "
+                       f"step 0 ({sample['t_rhs']:.2f} s) and {sample['iters']} PCG iterations "
+                       f"({sample['t_iter']:.2f} s each), scaled to {iters_per_step:.1f} iterations per step; "
+                       f"set-up excluded")}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+                except ValueError:
+                    pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [r for r in rows if r[2] > 250.0] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in load for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(load)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# FP64 FMA throughput measured on this machine's GB300 (register-resident FMA
+# chains, 152 x 16 blocks x 256 threads): 0.600 TFMA/s = 1.20 TFLOP/s.
+FP64_PEAK_GFLOPS = 1200.0
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    sample = None
+    if rank == 0 and not args.no_cpu_baseline:
+        sample = cpu_oracle_sample(args.n, args.cpu_iters)   # before any GPU work
+
+    from paper_2602_16312_gb300 import aggmg, build
+    build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    dev = torch.device("cuda")
+    wl = workload(args.n)
+    t0 = time.time()
+    mesh = aggmg.Mesh.from_workload(wl)
+    hier = aggmg.Hierarchy(mesh, 1.0 / wl.dt, wl.maps, precision=args.form)
+    setup_s = time.time() - t0
+    mask = torch.tensor(wl.stim_mask_nodal(), dtype=torch.float64, device=dev)
+    flexible = args.form != "f64"
+    sim = aggmg.Monodomain(hier, wl.dt, wl.ionic, iapp_mask=mask, iapp_value=wl.iapp_value,
+                           iapp_steps=wl.iapp_steps, rtol=wl.rtol, flexible=flexible)
+    N = wl.n_dofs
+    u = torch.zeros(N, dtype=torch.float64, device=dev)
+    w = torch.zeros(N, dtype=torch.float64, device=dev)
+    its_w = sim.step(u, w, args.warmup)                      # warm-up steps (stimulus on)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ev0.record(stream)
+        its = sim.step(u, w, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t = ev0.elapsed_time(ev1) / 1e3
+    if world > 1:
+        tt = torch.tensor([t], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    total_steps = args.steps * world
+    value = total_steps / t
+    # ---- end to end through the public API with pinned host state
+    uh = u.cpu().pin_memory()
+    wh = w.cpu().pin_memory()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    ev0.record(stream)
+    for _ in range(args.e2e_steps):
+        u.copy_(uh, non_blocking=True)
+        w.copy_(wh, non_blocking=True)
+        sim.step(u, w, 1)
+        uh.copy_(u, non_blocking=True)
+        wh.copy_(w, non_blocking=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = ev0.elapsed_time(ev1) / 1e3
+    del e0
+    # ---- dominant kernel, timed live with events on the launching stream
+    kid = 1
+    reps = 50
+    hier.profile_kernel(kid, 2)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    hier.profile_kernel(kid, reps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_k = ev0.elapsed_time(ev1) / 1e3 / reps
+    kbytes, kflops = hier.kernel_cost(kid)
+    ev0.record(stream)
+    hier.profile_kernel(0, reps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_k0 = ev0.elapsed_time(ev1) / 1e3 / reps
+    k0bytes, k0flops = hier.kernel_cost(0)
+    pk = peaks()
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    if kid == 1 and args.form == "f64":
+        roof = {"bound": "alu", "achieved": kflops / t_k / 1e9, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s"}
+    else:
+        roof = {"bound": "hbm", "achieved": kbytes / t_k / 1e9, "peak": hbm, "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = KERNEL_NAMES[kid]
+    roof["us_per_launch"] = t_k * 1e6
+    roof["algorithmic_bytes"] = kbytes
+    roof["peak_source"] = "MEASURED_PEAKS.json hbm_gbs (of measured)" if roof["bound"] == "hbm" else \
+        "measured FP64 FMA rate on GB300 (of measured)"
+    other = {"kernel": KERNEL_NAMES[0], "us_per_launch": t_k0 * 1e6,
+             "achieved_gflops": k0flops / t_k0 / 1e9, "fp64_peak_gflops": FP64_PEAK_GFLOPS,
+             "frac_fp64": k0flops / t_k0 / 1e9 / FP64_PEAK_GFLOPS,
+             "achieved_gbs": k0bytes / t_k0 / 1e9, "frac_hbm": k0bytes / t_k0 / 1e9 / hbm}
+    st = hier.stats()
+    L = hier.n_levels
+    vcyc = (L - 1) * 9 + 2
+    per_iter = 5 + vcyc + (1 if args.form != "f64" else 0)
+    n_iter = sum(its)
+    launches = args.steps * (1 + per_iter + 1) + n_iter * per_iter + 5
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 outer CG + " + {"f32": "f32 V-cycle", "f64": "f64 V-cycle",
+                                     "bf16s": "f32 V-cycle with bf16-stored smoother blocks"}[args.form],
+        "data": "synthetic",
+        "mdof_per_s": N * total_steps / t / 1e6,
+        "config": {"workload": workload_name(wl), "form": args.form, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (fine float64 matrix 0.85 GB, 129 MB L2)",
+                   "levels": st["units"], "op_complexity": st["op_complexity"], "setup_s": setup_s,
+                   "conditional_graph": True, "flexible_cg": flexible},
+        "iterations": {"mean": float(np.mean(its)), "min": int(min(its)), "max": int(max(its)),
+                       "std": float(np.std(its)), "warmup": its_w},
+        "e2e": {"value": args.e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * N * 8,
+                "d2h_bytes_per_step": 2 * N * 8},
+        "roofline": roof, "fine_fp64_spmv": other,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if sample is not None:
+        line["cpu_baseline"] = cpu_baseline_entry(sample, float(np.mean(its)), args.n)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sim.close()
+    hier.close()
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    sample = cpu_oracle_sample(args.n, args.cpu_iters)
+    # iterations per step of the float64 method on this workload (oracle, step 0)
+    iters = float(os.environ.get("AGG_REF_ITERS_PER_STEP", "39"))
+    base = cpu_baseline_entry(sample, iters, args.n)
+    t_step = 1.0 / base["value"]
+    steps = args.steps
+    from paper_2602_16312_gb300 import workloads as W
+    wl = W.jittered_square_2d(n=args.n, degree=2, n_levels=4)
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(wl), "form": "oracle f64"},
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

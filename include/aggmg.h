@@ -1,0 +1,239 @@
+/*
+ * aggmg.h - C ABI of libaggmg: agglomeration-based multigrid preconditioned
+ * CG for the SIPG discontinuous-Galerkin monodomain model, on one NVIDIA
+ * GB300 (sm_103a).
+ *
+ * The method (arXiv 2602.16312):
+ *   - monodomain model and ionic models: Section 2 (Eq. monodomain, the
+ *     FitzHugh-Nagumo model of Section 2.3.1);
+ *   - SIPG forms a_h, m_h and penalty: Section 3; linear system
+ *     A0 u^{n+1} = b with A0 = c M + A: Eq. fully_discrete;
+ *   - nested agglomerated levels, inherited operators
+ *     A_{l+1} = P^T A_l P: Section 5.1, Eq. inherited_matrices, Algorithm 3;
+ *   - Chebyshev-accelerated Jacobi smoother, one V-cycle per PCG iteration,
+ *     PCG warm-started from u^n: Section 6 (first paragraph), Section 3.1.
+ *
+ * Conventions for every call:
+ *   - Handles are opaque and owned by the library (free with *_destroy).
+ *   - `*_dev` arguments are device pointers owned by the caller (e.g. torch
+ *     tensors); the library never frees or reallocates them. Vectors are
+ *     float64, element-major: entry e*B + i is DoF i of element e, where
+ *     B = (p+1)^d and i = i0 + (p+1) i1 [+ (p+1)^2 i2] indexes the tensor GLL
+ *     nodes (x fastest). Coarse-level vectors use the caller's agglomerate
+ *     ids in the same unit-major layout.
+ *   - Host arrays passed to *_create / *_setup are copied; the caller may
+ *     free them afterwards.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Device work
+ *     is ordered on that stream; calls that return results to the host
+ *     (agg_pcg_solve, agg_monodomain_step) synchronise it.
+ *   - Every call returns an agg_status; nothing calls exit() or abort().
+ *     agg_last_error() returns a message for the calling thread's last error.
+ *   - A handle must not be used from two threads at once.
+ */
+#ifndef AGGMG_H
+#define AGGMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AGG_OK = 0,
+  AGG_EINVAL = -1,        /* invalid argument (sizes, pointers, maps)          */
+  AGG_ENOMEM = -2,        /* host or device allocation failed                  */
+  AGG_ECUDA = -3,         /* a CUDA runtime call failed                        */
+  AGG_ENOTSPD = -4,       /* a block or the coarsest matrix is not SPD         */
+  AGG_ENOTCONV = -5,      /* PCG reached max_it before the tolerance           */
+  AGG_ENAN = -6,          /* NaN or Inf in a residual norm                     */
+  AGG_EUNSUPPORTED = -7   /* a combination this build does not provide         */
+} agg_status;
+
+typedef struct agg_mesh* agg_mesh_t;
+typedef struct agg_hier* agg_hier_t;
+typedef struct agg_sim* agg_sim_t;
+
+/* ------------------------------------------------------------------ mesh
+ * Conforming quadrilateral (dim 2) or hexahedral (dim 3) mesh with
+ * multilinear element maps; corner c of an element sits at reference
+ * coordinates ((c>>0)&1, (c>>1)&1, (c>>2)&1). Neighbouring elements share
+ * vertex ids; a face of one element only is a boundary face (homogeneous
+ * Neumann, Section 2.2). Element matrices use Gauss-Legendre quadrature with
+ * p + 1 + quad_extra points per direction.
+ *
+ * SIPG penalty on an interior face F between K+ and K- (Section 3):
+ *   sigma = C_pen * max(|F|/|K+|, |F|/|K-|) * n^T ((D+ + D-)/2) n,
+ *   C_pen = p(p+1)                  if penalty_mode == 0 (the paper's alpha),
+ *   C_pen = penalty_coeff * p^2     if penalty_mode == 1.
+ */
+typedef struct {
+  int dim;                      /* 2 or 3                                        */
+  int degree;                   /* p in 1..4                                     */
+  int64_t n_vertices;
+  int64_t n_elements;
+  const double* vertices;       /* host [n_vertices][dim]                        */
+  const int64_t* elements;      /* host [n_elements][2^dim] vertex ids           */
+  const double* conductivity;   /* host [n_elements][dim][dim], symmetric SPD D  */
+  int penalty_mode;             /* 0 or 1, see above                             */
+  double penalty_coeff;
+  int quad_extra;               /* >= 0; 1 gives p+2 points per direction        */
+} agg_mesh_desc;
+
+/* Assembles, on the host in float64, the SIPG stiffness A and the element
+ * mass blocks M_e (Section 3, Eq. matrices). Errors: AGG_EINVAL for bad sizes
+ * or ids, a non-positive Jacobian or a non-conforming face. */
+agg_status agg_dg_mesh_create(const agg_mesh_desc* desc, agg_mesh_t* out);
+agg_status agg_dg_mesh_destroy(agg_mesh_t mesh);
+/* n_dofs = n_elements * (p+1)^dim; n_faces = number of interior faces. */
+agg_status agg_dg_mesh_info(agg_mesh_t mesh, int64_t* n_dofs, int64_t* n_faces);
+
+/* ------------------------------------------------------------------ hierarchy */
+enum { AGG_F64 = 0, AGG_F32 = 1, AGG_F32_BF16SMOOTH = 2 };
+
+typedef struct {
+  int n_levels;                  /* L >= 1 (1 = direct solve on level 0)        */
+  const int32_t* const* agg_maps;/* L-1 host maps; map l sends every level-l unit
+                                    to its level-(l+1) agglomerate in
+                                    [0, N_{l+1}); every id must be used         */
+  int smoother_degree;           /* Chebyshev degree (default 3)                 */
+  int block_jacobi;              /* 1: (p+1)^d blocks (default); 0: point Jacobi */
+  int lanczos_steps;             /* default 12                                   */
+  double cheb_upper_safety;      /* lambda_max = safety * Ritz max (default 1.2) */
+  double cheb_range;             /* lambda_min = lambda_max / range (default 20) */
+  int vcycle_precision;          /* AGG_F64, AGG_F32 or AGG_F32_BF16SMOOTH       */
+} agg_mg_opts;
+
+void agg_mg_opts_default(agg_mg_opts* opts);
+
+/* Algorithm 3 on the host in float64 with A0 = mass_coeff * M + A: bounding
+ * boxes of the agglomerates, prolongation blocks (nodal interpolation of the
+ * Q_p bounding-box basis, Section 5.1), Galerkin operators
+ * A_{l+1} = P^T A_l P (Eq. inherited_matrices), smoother blocks and their
+ * inverses, Lanczos bounds, Cholesky factor of the coarsest operator; then
+ * uploads everything to the current device in the requested precision and
+ * captures the solver's CUDA graphs. The device must stay the same for the
+ * handle's lifetime. Errors: AGG_EINVAL (maps), AGG_ENOTSPD, AGG_ENOMEM,
+ * AGG_ECUDA. */
+agg_status agg_mg_hierarchy_setup(agg_mesh_t mesh, double mass_coeff, const agg_mg_opts* opts,
+                                  void* stream, agg_hier_t* out);
+agg_status agg_mg_hierarchy_destroy(agg_hier_t hier);
+/* Per level l: units[l], block nonzeros nnzb[l] (pass arrays of n_levels
+ * entries or NULL), Chebyshev lambda_max[l] for l < L-1 (NULL allowed) and the
+ * operator complexity sum_l nnz(A_l) / nnz(A_0). */
+agg_status agg_hier_stats(agg_hier_t hier, int* n_levels, int64_t* units, int64_t* nnzb,
+                          double* lambda_max, double* op_complexity);
+
+/* ------------------------------------------------------------------ solve */
+typedef struct {
+  double rtol;     /* stop when ||r||_2 <= rtol ||r0||_2 ...                     */
+  double atol;     /* ... or ||r||_2 <= atol                                     */
+  int max_it;      /* limit on products A0 p; reaching it gives AGG_ENOTCONV     */
+  int flexible;    /* 1: Polak-Ribiere beta (safe with the float32 V-cycle)      */
+} agg_pcg_opts;
+
+typedef struct {
+  int iterations;  /* number of products A0 p                                     */
+  double r0_norm;
+  double r_norm;
+  int status;      /* agg_status of the solve                                     */
+} agg_pcg_result;
+
+/* PCG on A0 x = b preconditioned by one V-cycle per iteration (Section 6),
+ * x_dev holds the initial guess on entry and the solution on return. The
+ * outer recurrence, dot products and x are float64 in every precision form.
+ * Synchronises `stream`. Returns AGG_ENOTCONV / AGG_ENAN as the result's
+ * status too. */
+agg_status agg_pcg_solve(agg_hier_t hier, const double* b_dev, double* x_dev,
+                         const agg_pcg_opts* opts, agg_pcg_result* res, void* stream);
+/* y = A_l x with the level's stored operator (float64 on level 0 always;
+ * levels >= 1 in the V-cycle precision, converted from/to float64). */
+agg_status agg_operator_apply(agg_hier_t hier, int level, const double* x_dev, double* y_dev,
+                              void* stream);
+/* z = B r: one V-cycle of the preconditioner (Section 6). */
+agg_status agg_vcycle_apply(agg_hier_t hier, const double* r_dev, double* z_dev, void* stream);
+
+/* ------------------------------------------------------------------ ionic models */
+typedef enum { AGG_FHN = 0, AGG_ALIEV_PANFILOV = 1 } agg_ionic_model;
+
+/* FitzHugh-Nagumo (Section 2.3.1): I = k u (u-a)(u-1) + w, H = eps (u - gamma w).
+ * Aliev-Panfilov (not in the paper; published 1996 form):
+ *   I = k u (u-a)(u-1) + u w, H = (eps + mu1 w/(u+mu2)) (-w - k u (u-a-1)). */
+typedef struct {
+  int model;
+  double k, a, eps, gamma, mu1, mu2;
+} agg_ionic_params;
+
+/* w <- w + dt H(u, w) at n DoFs (forward Euler; Section 3.1, first bullet). */
+agg_status agg_ionic_update(const agg_ionic_params* prm, double dt, int64_t n, const double* u_dev,
+                            double* w_dev, void* stream);
+
+/* ------------------------------------------------------------------ time stepping */
+typedef struct {
+  double dt, chi_m, c_m;          /* mass coefficient must equal chi_m c_m / dt  */
+  agg_ionic_params ionic;
+  const double* iapp_mask_dev;    /* [n_dofs] nodal stimulus mask (copied)        */
+  double iapp_value;              /* I_app = iapp_value * mask for the first      */
+  int iapp_steps;                 /* iapp_steps steps, zero afterwards            */
+  agg_pcg_opts pcg;
+} agg_sim_opts;
+
+/* One step n -> n+1 (Section 3.1 with the backward-Euler form of
+ * Eq. fully_discrete and ionic current interpolation):
+ *   w^{n+1} = w^n + dt H(u^n, w^n)
+ *   b = M (c u^n + I_app(t_{n+1}) - chi_m I_ion(u^n, w^{n+1})),  c = chi_m c_m/dt
+ *   A0 u^{n+1} = b by PCG warm-started from u^n. */
+agg_status agg_monodomain_create(agg_hier_t hier, const agg_sim_opts* opts, agg_sim_t* out);
+/* Advances n_steps steps in place on u_dev, w_dev ([n_dofs] each); the
+ * stimulus clock is the handle's step counter (starts at 0). iters_out: host
+ * array of n_steps PCG iteration counts, or NULL. Synchronises `stream`. */
+agg_status agg_monodomain_step(agg_sim_t sim, int n_steps, double* u_dev, double* w_dev,
+                               int* iters_out, void* stream);
+agg_status agg_monodomain_set_clock(agg_sim_t sim, int64_t step);
+agg_status agg_monodomain_destroy(agg_sim_t sim);
+
+/* ------------------------------------------------------------------ instrumentation
+ * Kernel ids: 0 fine float64 SpMV y = A0 x (the outer CG's operator),
+ * 1 fine Chebyshev step in the V-cycle precision (SpMV + residual + block
+ * inverse + two axpys), 2 fine residual + restriction, 3 fine prolongation.
+ * agg_profile_kernel launches the kernel `reps` times on the hierarchy's own
+ * work buffers (valid after any solve or V-cycle) on `stream`, so a caller
+ * can time it with events; agg_kernel_cost gives its algorithmic HBM bytes
+ * (every matrix, block and vector entry read or written once) and flops per
+ * launch. */
+agg_status agg_profile_kernel(agg_hier_t hier, int kernel, int reps, void* stream);
+agg_status agg_kernel_cost(agg_hier_t hier, int kernel, double* bytes, double* flops);
+
+/* ------------------------------------------------------------------ host inspection
+ * Host-only access to the float64 set-up (no device needed), for checking
+ * the assembly and Algorithm 3 against an independent implementation.
+ * agg_dg_mesh_copy `what`: 0 stiffness row pointers (int64, n_elements+1),
+ * 1 block columns (int32, nnzb), 2 blocks (float64, nnzb*B*B, row-major
+ * blocks), 3 element mass blocks (float64, n_elements*B*B), 4 element
+ * volumes (float64, n_elements). The stiffness excludes the mass term. */
+agg_status agg_dg_mesh_copy(agg_mesh_t mesh, int what, void* dst);
+agg_status agg_dg_mesh_nnzb(agg_mesh_t mesh, int64_t* nnzb);
+
+typedef struct agg_host_hier* agg_host_hier_t;
+/* Runs the host part of agg_mg_hierarchy_setup (same arguments, no upload). */
+agg_status agg_host_hierarchy_build(agg_mesh_t mesh, double mass_coeff, const agg_mg_opts* opts,
+                                    agg_host_hier_t* out);
+agg_status agg_host_hierarchy_destroy(agg_host_hier_t hh);
+/* Level l: units, block nonzeros, lambda_max (0 on the coarsest). */
+agg_status agg_host_hierarchy_level(agg_host_hier_t hh, int level, int64_t* n_units, int64_t* nnzb,
+                                    double* lambda_max);
+/* Copies level data in the library's internal unit order. `what`:
+ * 0 perm (int64, n: internal index -> caller's id), 1 row pointers (int64,
+ * n+1), 2 block columns (int32, nnzb, internal indices), 3 blocks (float64,
+ * nnzb*B*B row-major), 4 smoother block inverses (float64, n*B*B),
+ * 5 prolongation blocks to level l+1 (float64, n*B*B, P[u][i][j] =
+ * coarse basis j at node i), 6 parent (int32, n, internal index on l+1). */
+agg_status agg_host_hierarchy_copy(agg_host_hier_t hh, int level, int what, void* dst);
+
+const char* agg_status_string(int status);
+const char* agg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AGGMG_H */

@@ -1,0 +1,369 @@
+"""ctypes binding of libaggmg (include/aggmg.h): argument marshalling only.
+
+Every computation runs in the library; this module converts numpy arrays
+(host inputs) and torch tensors (device vectors, via data_ptr()) to the C
+ABI, and raises AggError on a non-zero status. The library must have been
+built (`paper_2602_16312_gb300.build.build()`); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+AGG_OK, AGG_EINVAL, AGG_ENOMEM, AGG_ECUDA, AGG_ENOTSPD, AGG_ENOTCONV, AGG_ENAN, AGG_EUNSUPPORTED = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+AGG_F64, AGG_F32, AGG_F32_BF16SMOOTH = 0, 1, 2
+PRECISIONS = {"f64": AGG_F64, "f32": AGG_F32, "bf16s": AGG_F32_BF16SMOOTH}
+AGG_FHN, AGG_ALIEV_PANFILOV = 0, 1
+
+
+class AggError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("degree", C.c_int), ("n_vertices", C.c_int64), ("n_elements", C.c_int64),
+                ("vertices", C.POINTER(C.c_double)), ("elements", C.POINTER(C.c_int64)),
+                ("conductivity", C.POINTER(C.c_double)), ("penalty_mode", C.c_int),
+                ("penalty_coeff", C.c_double), ("quad_extra", C.c_int)]
+
+
+class MGOpts(C.Structure):
+    _fields_ = [("n_levels", C.c_int), ("agg_maps", C.POINTER(C.POINTER(C.c_int32))),
+                ("smoother_degree", C.c_int), ("block_jacobi", C.c_int), ("lanczos_steps", C.c_int),
+                ("cheb_upper_safety", C.c_double), ("cheb_range", C.c_double), ("vcycle_precision", C.c_int)]
+
+
+class PCGOpts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("max_it", C.c_int), ("flexible", C.c_int)]
+
+
+class PCGResult(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("r0_norm", C.c_double), ("r_norm", C.c_double), ("status", C.c_int)]
+
+
+class IonicParams(C.Structure):
+    _fields_ = [("model", C.c_int), ("k", C.c_double), ("a", C.c_double), ("eps", C.c_double),
+                ("gamma", C.c_double), ("mu1", C.c_double), ("mu2", C.c_double)]
+
+
+class SimOpts(C.Structure):
+    _fields_ = [("dt", C.c_double), ("chi_m", C.c_double), ("c_m", C.c_double), ("ionic", IonicParams),
+                ("iapp_mask_dev", C.c_void_p), ("iapp_value", C.c_double), ("iapp_steps", C.c_int),
+                ("pcg", PCGOpts)]
+
+
+_lib = None
+
+_SIGS = {
+    "agg_dg_mesh_create": [C.POINTER(MeshDesc), C.POINTER(C.c_void_p)],
+    "agg_dg_mesh_destroy": [C.c_void_p],
+    "agg_dg_mesh_info": [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+    "agg_dg_mesh_nnzb": [C.c_void_p, C.POINTER(C.c_int64)],
+    "agg_dg_mesh_copy": [C.c_void_p, C.c_int, C.c_void_p],
+    "agg_mg_opts_default": [C.POINTER(MGOpts)],
+    "agg_mg_hierarchy_setup": [C.c_void_p, C.c_double, C.POINTER(MGOpts), C.c_void_p, C.POINTER(C.c_void_p)],
+    "agg_mg_hierarchy_destroy": [C.c_void_p],
+    "agg_hier_stats": [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                       C.POINTER(C.c_double), C.POINTER(C.c_double)],
+    "agg_pcg_solve": [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(PCGOpts), C.POINTER(PCGResult), C.c_void_p],
+    "agg_operator_apply": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p],
+    "agg_vcycle_apply": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "agg_ionic_update": [C.POINTER(IonicParams), C.c_double, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
+    "agg_monodomain_create": [C.c_void_p, C.POINTER(SimOpts), C.POINTER(C.c_void_p)],
+    "agg_monodomain_step": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.c_void_p],
+    "agg_monodomain_set_clock": [C.c_void_p, C.c_int64],
+    "agg_monodomain_destroy": [C.c_void_p],
+    "agg_host_hierarchy_build": [C.c_void_p, C.c_double, C.POINTER(MGOpts), C.POINTER(C.c_void_p)],
+    "agg_host_hierarchy_destroy": [C.c_void_p],
+    "agg_host_hierarchy_level": [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                 C.POINTER(C.c_double)],
+    "agg_host_hierarchy_copy": [C.c_void_p, C.c_int, C.c_int, C.c_void_p],
+    "agg_profile_kernel": [C.c_void_p, C.c_int, C.c_int, C.c_void_p],
+    "agg_kernel_cost": [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+    "agg_status_string": [C.c_int],
+    "agg_last_error": [],
+}
+
+
+def lib():
+    """Loads libaggmg.so from the package's build folder (raises if absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libaggmg.so is not built ({path}); run paper_2602_16312_gb300.build.build()")
+    L = C.CDLL(path)
+    for name, args in _SIGS.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    L.agg_status_string.restype = C.c_char_p
+    L.agg_last_error.restype = C.c_char_p
+    L.agg_mg_opts_default.restype = None
+    _lib = L
+    return L
+
+
+def exported_symbols() -> List[str]:
+    return list(_SIGS)
+
+
+def _check(status):
+    if status != AGG_OK:
+        msg = lib().agg_last_error().decode(errors="replace")
+        raise AggError(status, msg or lib().agg_status_string(status).decode())
+
+
+def _dptr(t) -> int:
+    """Device pointer of a contiguous float64 CUDA tensor."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float64 tensor")
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+# ---------------------------------------------------------------- mesh
+class Mesh:
+    """agg_dg_mesh_create: SIPG stiffness and element mass blocks (host FP64)."""
+
+    def __init__(self, vertices, elements, conductivity, degree, penalty_mode=1, penalty_coeff=10.0,
+                 quad_extra=1):
+        self.vertices = np.ascontiguousarray(vertices, dtype=np.float64)
+        self.elements = np.ascontiguousarray(elements, dtype=np.int64)
+        self.conductivity = np.ascontiguousarray(conductivity, dtype=np.float64)
+        self.dim = self.vertices.shape[1]
+        self.degree = degree
+        self.B = (degree + 1) ** self.dim
+        self.n_elements = self.elements.shape[0]
+        d = MeshDesc(self.dim, degree, self.vertices.shape[0], self.n_elements,
+                     self.vertices.ctypes.data_as(C.POINTER(C.c_double)),
+                     self.elements.ctypes.data_as(C.POINTER(C.c_int64)),
+                     self.conductivity.ctypes.data_as(C.POINTER(C.c_double)),
+                     penalty_mode, penalty_coeff, quad_extra)
+        h = C.c_void_p()
+        _check(lib().agg_dg_mesh_create(C.byref(d), C.byref(h)))
+        self.handle = h
+
+    @classmethod
+    def from_workload(cls, wl):
+        return cls(wl.mesh.vertices, wl.mesh.elements, wl.conductivity, wl.degree, wl.penalty_mode,
+                   wl.penalty_coeff)
+
+    @property
+    def n_dofs(self):
+        return self.n_elements * self.B
+
+    def info(self):
+        nd, nf = C.c_int64(), C.c_int64()
+        _check(lib().agg_dg_mesh_info(self.handle, C.byref(nd), C.byref(nf)))
+        return nd.value, nf.value
+
+    def stiffness_bsr(self):
+        """(rowptr, cols, blocks) of the SIPG stiffness in element order."""
+        nnzb = C.c_int64()
+        _check(lib().agg_dg_mesh_nnzb(self.handle, C.byref(nnzb)))
+        rp = np.empty(self.n_elements + 1, np.int64)
+        cols = np.empty(nnzb.value, np.int32)
+        vals = np.empty((nnzb.value, self.B, self.B), np.float64)
+        for what, arr in ((0, rp), (1, cols), (2, vals)):
+            _check(lib().agg_dg_mesh_copy(self.handle, what, arr.ctypes.data))
+        return rp, cols, vals
+
+    def element_mass(self):
+        out = np.empty((self.n_elements, self.B, self.B))
+        _check(lib().agg_dg_mesh_copy(self.handle, 3, out.ctypes.data))
+        return out
+
+    def volumes(self):
+        out = np.empty(self.n_elements)
+        _check(lib().agg_dg_mesh_copy(self.handle, 4, out.ctypes.data))
+        return out
+
+    def close(self):
+        if self.handle:
+            lib().agg_dg_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _mg_opts(maps: Sequence[np.ndarray], precision="f64", block_jacobi=True, lanczos_steps=12,
+             safety=1.2, cheb_range=20.0):
+    o = MGOpts()
+    lib().agg_mg_opts_default(C.byref(o))
+    keep = [np.ascontiguousarray(m, dtype=np.int32) for m in maps]
+    arr = (C.POINTER(C.c_int32) * max(1, len(keep)))()
+    for i, m in enumerate(keep):
+        arr[i] = m.ctypes.data_as(C.POINTER(C.c_int32))
+    o.n_levels = len(keep) + 1
+    o.agg_maps = C.cast(arr, C.POINTER(C.POINTER(C.c_int32)))
+    o.block_jacobi = int(block_jacobi)
+    o.lanczos_steps = lanczos_steps
+    o.cheb_upper_safety = safety
+    o.cheb_range = cheb_range
+    o.vcycle_precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return o, (keep, arr)
+
+
+class HostHierarchy:
+    """agg_host_hierarchy_build: the float64 set-up without a device."""
+
+    def __init__(self, mesh: Mesh, mass_coeff: float, maps, **kw):
+        o, self._keep = _mg_opts(maps, **kw)
+        h = C.c_void_p()
+        _check(lib().agg_host_hierarchy_build(mesh.handle, mass_coeff, C.byref(o), C.byref(h)))
+        self.handle = h
+        self.B = mesh.B
+        self.n_levels = o.n_levels
+
+    def level(self, l):
+        n, nnzb, lam = C.c_int64(), C.c_int64(), C.c_double()
+        _check(lib().agg_host_hierarchy_level(self.handle, l, C.byref(n), C.byref(nnzb), C.byref(lam)))
+        return n.value, nnzb.value, lam.value
+
+    def copy(self, l, what):
+        n, nnzb, _ = self.level(l)
+        B = self.B
+        spec = {0: (np.int64, (n,)), 1: (np.int64, (n + 1,)), 2: (np.int32, (nnzb,)),
+                3: (np.float64, (nnzb, B, B)), 4: (np.float64, (n, B, B)), 5: (np.float64, (n, B, B)),
+                6: (np.int32, (n,))}[what]
+        out = np.empty(spec[1], spec[0])
+        _check(lib().agg_host_hierarchy_copy(self.handle, l, what, out.ctypes.data))
+        return out
+
+    def close(self):
+        if self.handle:
+            lib().agg_host_hierarchy_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Hierarchy:
+    """agg_mg_hierarchy_setup: host set-up + upload + CUDA graphs."""
+
+    def __init__(self, mesh: Mesh, mass_coeff: float, maps, precision="f64", stream=None, **kw):
+        o, self._keep = _mg_opts(maps, precision=precision, **kw)
+        h = C.c_void_p()
+        _check(lib().agg_mg_hierarchy_setup(mesh.handle, mass_coeff, C.byref(o), C.c_void_p(_stream(stream)),
+                                            C.byref(h)))
+        self.handle = h
+        self.mesh = mesh
+        self.n_levels = o.n_levels
+        self.mass_coeff = mass_coeff
+
+    def stats(self):
+        L = self.n_levels
+        units = (C.c_int64 * L)()
+        nnzb = (C.c_int64 * L)()
+        lam = (C.c_double * L)()
+        oc = C.c_double()
+        nl = C.c_int()
+        _check(lib().agg_hier_stats(self.handle, C.byref(nl), units, nnzb, lam, C.byref(oc)))
+        return dict(units=list(units), nnzb=list(nnzb), lambda_max=list(lam)[:L - 1], op_complexity=oc.value)
+
+    def pcg_solve(self, b, x, rtol=1e-8, atol=0.0, max_it=500, flexible=False, stream=None, check=True):
+        o = PCGOpts(rtol, atol, max_it, int(flexible))
+        r = PCGResult()
+        st = lib().agg_pcg_solve(self.handle, C.c_void_p(_dptr(b)), C.c_void_p(_dptr(x)), C.byref(o),
+                                 C.byref(r), C.c_void_p(_stream(stream)))
+        if check and st not in (AGG_OK,):
+            _check(st)
+        return dict(iterations=r.iterations, r0_norm=r.r0_norm, r_norm=r.r_norm, status=r.status)
+
+    def operator_apply(self, level, x, y, stream=None):
+        _check(lib().agg_operator_apply(self.handle, level, C.c_void_p(_dptr(x)), C.c_void_p(_dptr(y)),
+                                        C.c_void_p(_stream(stream))))
+
+    def vcycle_apply(self, r, z, stream=None):
+        _check(lib().agg_vcycle_apply(self.handle, C.c_void_p(_dptr(r)), C.c_void_p(_dptr(z)),
+                                      C.c_void_p(_stream(stream))))
+
+    def profile_kernel(self, kernel, reps, stream=None):
+        _check(lib().agg_profile_kernel(self.handle, kernel, reps, C.c_void_p(_stream(stream))))
+
+    def kernel_cost(self, kernel):
+        b, f = C.c_double(), C.c_double()
+        _check(lib().agg_kernel_cost(self.handle, kernel, C.byref(b), C.byref(f)))
+        return b.value, f.value
+
+    def close(self):
+        if self.handle:
+            lib().agg_mg_hierarchy_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ionic_params(d: dict) -> IonicParams:
+    return IonicParams(int(d["model"]), d["k"], d["a"], d["eps"], d.get("gamma", 0.0), d.get("mu1", 0.0),
+                       d.get("mu2", 0.0))
+
+
+def ionic_update(prm: dict, dt: float, u, w, stream=None):
+    p = ionic_params(prm)
+    _check(lib().agg_ionic_update(C.byref(p), dt, u.numel(), C.c_void_p(_dptr(u)), C.c_void_p(_dptr(w)),
+                                  C.c_void_p(_stream(stream))))
+
+
+class Monodomain:
+    """agg_monodomain_create / agg_monodomain_step on a hierarchy."""
+
+    def __init__(self, hier: Hierarchy, dt, ionic: dict, iapp_mask=None, iapp_value=1.0, iapp_steps=5,
+                 rtol=1e-8, atol=0.0, max_it=500, flexible=False, chi_m=1.0, c_m=1.0):
+        self._mask = iapp_mask
+        o = SimOpts(dt, chi_m, c_m, ionic_params(ionic), C.c_void_p(_dptr(iapp_mask)) if iapp_mask is not None
+                    else None, iapp_value, iapp_steps, PCGOpts(rtol, atol, max_it, int(flexible)))
+        h = C.c_void_p()
+        _check(lib().agg_monodomain_create(hier.handle, C.byref(o), C.byref(h)))
+        self.handle = h
+        self.hier = hier
+
+    def step(self, u, w, n_steps=1, stream=None, iters=True):
+        its = (C.c_int * n_steps)() if iters else None
+        _check(lib().agg_monodomain_step(self.handle, n_steps, C.c_void_p(_dptr(u)), C.c_void_p(_dptr(w)),
+                                         its, C.c_void_p(_stream(stream))))
+        return list(its) if iters else None
+
+    def set_clock(self, step):
+        _check(lib().agg_monodomain_set_clock(self.handle, step))
+
+    def close(self):
+        if self.handle:
+            lib().agg_monodomain_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,461 @@
+// C ABI of libaggmg (declared in include/aggmg.h): argument checking, the
+// host set-up calls and dispatch to the per-block-size device engines.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+
+#include "../../include/aggmg.h"
+#include "cg_kernels.cuh"
+#include "engine.h"
+#include "setup.h"
+
+namespace aggmg {
+EngineBase* make_engine_b4(int);
+EngineBase* make_engine_b8(int);
+EngineBase* make_engine_b9(int);
+EngineBase* make_engine_b16(int);
+EngineBase* make_engine_b27(int);
+
+EngineBase* make_engine(int B, int precision) {
+  switch (B) {
+    case 4: return make_engine_b4(precision);
+    case 8: return make_engine_b8(precision);
+    case 9: return make_engine_b9(precision);
+    case 16: return make_engine_b16(precision);
+    case 27: return make_engine_b27(precision);
+    default: return nullptr;
+  }
+}
+}  // namespace aggmg
+
+using namespace aggmg;
+
+struct agg_mesh {
+  Mesh m;
+};
+
+struct agg_hier {
+  agg_mesh* mesh = nullptr;
+  int device = 0;
+  int L = 0, B = 0, precision = 0;
+  double mass_coeff = 0;
+  std::vector<int64_t> units, nnzb, perm0;
+  std::vector<double> lam_max;
+  EngineBase* eng = nullptr;
+  bool sim_active = false;
+};
+
+struct agg_sim {
+  agg_hier* h = nullptr;
+  int64_t clock = 0;
+};
+
+namespace {
+thread_local std::string g_err;
+
+agg_status fail(agg_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+agg_status check_device(const agg_hier* h) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(AGG_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev != h->device) return fail(AGG_EINVAL, "current device differs from the hierarchy's device");
+  return AGG_OK;
+}
+}  // namespace
+
+extern "C" {
+
+const char* agg_last_error(void) { return g_err.c_str(); }
+
+const char* agg_status_string(int s) {
+  switch (s) {
+    case AGG_OK: return "ok";
+    case AGG_EINVAL: return "invalid argument";
+    case AGG_ENOMEM: return "out of memory";
+    case AGG_ECUDA: return "CUDA error";
+    case AGG_ENOTSPD: return "matrix not symmetric positive definite";
+    case AGG_ENOTCONV: return "PCG did not converge within max_it";
+    case AGG_ENAN: return "NaN or Inf in the residual";
+    case AGG_EUNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+agg_status agg_dg_mesh_create(const agg_mesh_desc* d, agg_mesh_t* out) {
+  if (!d || !out) return fail(AGG_EINVAL, "NULL argument");
+  if (!d->vertices || !d->elements || !d->conductivity) return fail(AGG_EINVAL, "NULL mesh array");
+  if (d->n_vertices <= 0 || d->n_elements <= 0) return fail(AGG_EINVAL, "empty mesh");
+  if (d->dim != 2 && d->dim != 3) return fail(AGG_EINVAL, "dim must be 2 or 3");
+  if (d->penalty_mode != 0 && d->penalty_mode != 1) return fail(AGG_EINVAL, "penalty_mode must be 0 or 1");
+  std::unique_ptr<agg_mesh> mh;
+  try {
+    mh.reset(new agg_mesh());
+    Mesh& m = mh->m;
+    m.dim = d->dim;
+    m.p = d->degree;
+    m.nv = d->n_vertices;
+    m.ne = d->n_elements;
+    const int V = 1 << d->dim;
+    m.X.assign(d->vertices, d->vertices + d->n_vertices * d->dim);
+    m.cells.assign(d->elements, d->elements + d->n_elements * V);
+    m.D.assign(d->conductivity, d->conductivity + d->n_elements * d->dim * d->dim);
+    m.penalty_mode = d->penalty_mode;
+    m.penalty_coeff = d->penalty_coeff;
+    m.quad_extra = d->quad_extra;
+    std::string err;
+    int s = mesh_build(m, err);
+    if (s) return fail((agg_status)s, err);
+  } catch (const std::bad_alloc&) {
+    return fail(AGG_ENOMEM, "host allocation failed");
+  }
+  *out = mh.release();
+  return AGG_OK;
+}
+
+agg_status agg_dg_mesh_destroy(agg_mesh_t m) {
+  delete m;
+  return AGG_OK;
+}
+
+agg_status agg_dg_mesh_info(agg_mesh_t m, int64_t* n_dofs, int64_t* n_faces) {
+  if (!m) return fail(AGG_EINVAL, "NULL mesh");
+  if (n_dofs) *n_dofs = m->m.ne * m->m.B;
+  if (n_faces) *n_faces = m->m.n_faces;
+  return AGG_OK;
+}
+
+agg_status agg_dg_mesh_nnzb(agg_mesh_t m, int64_t* nnzb) {
+  if (!m || !nnzb) return fail(AGG_EINVAL, "NULL argument");
+  *nnzb = m->m.A.nnzb();
+  return AGG_OK;
+}
+
+agg_status agg_dg_mesh_copy(agg_mesh_t mh, int what, void* dst) {
+  if (!mh || !dst) return fail(AGG_EINVAL, "NULL argument");
+  const Mesh& m = mh->m;
+  switch (what) {
+    case 0: std::memcpy(dst, m.A.rowptr.data(), sizeof(int64_t) * m.A.rowptr.size()); break;
+    case 1: std::memcpy(dst, m.A.col.data(), sizeof(int32_t) * m.A.col.size()); break;
+    case 2: std::memcpy(dst, m.A.val.data(), sizeof(double) * m.A.val.size()); break;
+    case 3: std::memcpy(dst, m.Me.data(), sizeof(double) * m.Me.size()); break;
+    case 4: std::memcpy(dst, m.vol.data(), sizeof(double) * m.vol.size()); break;
+    default: return fail(AGG_EINVAL, "what");
+  }
+  return AGG_OK;
+}
+
+void agg_mg_opts_default(agg_mg_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->n_levels = 1;
+  o->smoother_degree = 3;
+  o->block_jacobi = 1;
+  o->lanczos_steps = 12;
+  o->cheb_upper_safety = 1.2;
+  o->cheb_range = 20.0;
+  o->vcycle_precision = AGG_F64;
+}
+
+static agg_status check_mg_opts(const agg_mg_opts* o, double mass_coeff);
+static HierOptions host_options(const agg_mg_opts* o);
+
+agg_status agg_mg_hierarchy_setup(agg_mesh_t mesh, double mass_coeff, const agg_mg_opts* o, void* stream,
+                                  agg_hier_t* out) {
+  if (!mesh || !out) return fail(AGG_EINVAL, "NULL argument");
+  agg_status chk = check_mg_opts(o, mass_coeff);
+  if (chk) return chk;
+  if (o->n_levels < 2) return fail(AGG_EUNSUPPORTED, "the device solver needs n_levels >= 2");
+  const Mesh& m = mesh->m;
+  std::unique_ptr<agg_hier> h(new agg_hier());
+  h->mesh = mesh;
+  cudaError_t ce = cudaGetDevice(&h->device);
+  if (ce != cudaSuccess) return fail(AGG_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(ce));
+  h->L = o->n_levels;
+  h->B = m.B;
+  h->precision = o->vcycle_precision;
+  h->mass_coeff = mass_coeff;
+  std::unique_ptr<EngineBase> eng(make_engine(m.B, o->vcycle_precision));
+  if (!eng) return fail(AGG_EUNSUPPORTED, "no engine for this element block size (B = " + std::to_string(m.B) + ")");
+  std::string err;
+  try {
+    HostHierarchy hh;
+    int s = hierarchy_build(m, mass_coeff, host_options(o), hh, err);
+    if (s) return fail((agg_status)s, err);
+    for (int l = 0; l < hh.L; ++l) {
+      h->units.push_back(hh.lev[l].n);
+      h->nnzb.push_back(hh.lev[l].A.nnzb());
+      h->lam_max.push_back(hh.lev[l].lam_max);
+    }
+    h->perm0 = hh.lev[0].perm;
+    s = eng->init(hh, m, o->vcycle_precision, (cudaStream_t)stream, err);
+    if (s) return fail((agg_status)s, err);
+  } catch (const std::bad_alloc&) {
+    return fail(AGG_ENOMEM, "host allocation failed");
+  }
+  h->eng = eng.release();
+  *out = h.release();
+  return AGG_OK;
+}
+
+agg_status agg_mg_hierarchy_destroy(agg_hier_t h) {
+  if (!h) return AGG_OK;
+  delete h->eng;
+  delete h;
+  return AGG_OK;
+}
+
+agg_status agg_hier_stats(agg_hier_t h, int* n_levels, int64_t* units, int64_t* nnzb, double* lambda_max,
+                          double* op_complexity) {
+  if (!h) return fail(AGG_EINVAL, "NULL hierarchy");
+  if (n_levels) *n_levels = h->L;
+  double tot = 0;
+  for (int l = 0; l < h->L; ++l) {
+    if (units) units[l] = h->units[l];
+    if (nnzb) nnzb[l] = h->nnzb[l];
+    if (lambda_max && l + 1 < h->L) lambda_max[l] = h->lam_max[l];
+    tot += (double)h->nnzb[l];
+  }
+  if (op_complexity) *op_complexity = tot / (double)h->nnzb[0];
+  return AGG_OK;
+}
+
+struct agg_host_hier {
+  HostHierarchy h;
+};
+
+static agg_status check_mg_opts(const agg_mg_opts* o, double mass_coeff) {
+  if (!o) return fail(AGG_EINVAL, "NULL options");
+  if (o->n_levels < 1) return fail(AGG_EINVAL, "n_levels must be >= 1");
+  if (o->n_levels > 1 && !o->agg_maps) return fail(AGG_EINVAL, "agg_maps is NULL");
+  if (o->smoother_degree != 3) return fail(AGG_EUNSUPPORTED, "smoother_degree must be 3");
+  if (o->vcycle_precision < AGG_F64 || o->vcycle_precision > AGG_F32_BF16SMOOTH)
+    return fail(AGG_EINVAL, "vcycle_precision");
+  if (!(o->cheb_upper_safety > 0) || !(o->cheb_range > 1) || o->lanczos_steps < 1)
+    return fail(AGG_EINVAL, "Chebyshev options");
+  if (!(mass_coeff >= 0) || !std::isfinite(mass_coeff)) return fail(AGG_EINVAL, "mass_coeff");
+  return AGG_OK;
+}
+
+static HierOptions host_options(const agg_mg_opts* o) {
+  HierOptions ho;
+  ho.L = o->n_levels;
+  ho.maps = o->agg_maps;
+  ho.degree = o->smoother_degree;
+  ho.block_jacobi = o->block_jacobi != 0;
+  ho.lanczos_steps = o->lanczos_steps;
+  ho.safety = o->cheb_upper_safety;
+  ho.range = o->cheb_range;
+  return ho;
+}
+
+agg_status agg_host_hierarchy_build(agg_mesh_t mesh, double mass_coeff, const agg_mg_opts* o, agg_host_hier_t* out) {
+  if (!mesh || !out) return fail(AGG_EINVAL, "NULL argument");
+  agg_status s = check_mg_opts(o, mass_coeff);
+  if (s) return s;
+  std::unique_ptr<agg_host_hier> hh;
+  try {
+    hh.reset(new agg_host_hier());
+    std::string err;
+    int rc = hierarchy_build(mesh->m, mass_coeff, host_options(o), hh->h, err);
+    if (rc) return fail((agg_status)rc, err);
+  } catch (const std::bad_alloc&) {
+    return fail(AGG_ENOMEM, "host allocation failed");
+  }
+  *out = hh.release();
+  return AGG_OK;
+}
+
+agg_status agg_host_hierarchy_destroy(agg_host_hier_t hh) {
+  delete hh;
+  return AGG_OK;
+}
+
+agg_status agg_host_hierarchy_level(agg_host_hier_t hh, int l, int64_t* n, int64_t* nnzb, double* lam) {
+  if (!hh || l < 0 || l >= hh->h.L) return fail(AGG_EINVAL, "level");
+  const HostLevel& v = hh->h.lev[l];
+  if (n) *n = v.n;
+  if (nnzb) *nnzb = v.A.nnzb();
+  if (lam) *lam = v.lam_max;
+  return AGG_OK;
+}
+
+agg_status agg_host_hierarchy_copy(agg_host_hier_t hh, int l, int what, void* dst) {
+  if (!hh || !dst || l < 0 || l >= hh->h.L) return fail(AGG_EINVAL, "bad argument");
+  const HostLevel& v = hh->h.lev[l];
+  switch (what) {
+    case 0: std::memcpy(dst, v.perm.data(), sizeof(int64_t) * v.perm.size()); break;
+    case 1: std::memcpy(dst, v.A.rowptr.data(), sizeof(int64_t) * v.A.rowptr.size()); break;
+    case 2: std::memcpy(dst, v.A.col.data(), sizeof(int32_t) * v.A.col.size()); break;
+    case 3: std::memcpy(dst, v.A.val.data(), sizeof(double) * v.A.val.size()); break;
+    case 4:
+      if (v.Dinv.empty()) return fail(AGG_EINVAL, "no smoother on the coarsest level");
+      std::memcpy(dst, v.Dinv.data(), sizeof(double) * v.Dinv.size());
+      break;
+    case 5:
+      if (v.P.empty()) return fail(AGG_EINVAL, "no prolongation from the coarsest level");
+      std::memcpy(dst, v.P.data(), sizeof(double) * v.P.size());
+      break;
+    case 6:
+      if (v.parent.empty()) return fail(AGG_EINVAL, "no parent on the coarsest level");
+      std::memcpy(dst, v.parent.data(), sizeof(int32_t) * v.parent.size());
+      break;
+    default: return fail(AGG_EINVAL, "what");
+  }
+  return AGG_OK;
+}
+
+static agg_status check_pcg_opts(const agg_pcg_opts* o) {
+  if (!o) return fail(AGG_EINVAL, "NULL pcg options");
+  if (!(o->rtol >= 0) || !(o->atol >= 0) || o->max_it < 1) return fail(AGG_EINVAL, "pcg options");
+  return AGG_OK;
+}
+
+agg_status agg_pcg_solve(agg_hier_t h, const double* b, double* x, const agg_pcg_opts* o, agg_pcg_result* res,
+                         void* stream) {
+  if (!h || !b || !x) return fail(AGG_EINVAL, "NULL argument");
+  agg_status s = check_pcg_opts(o);
+  if (s) return s;
+  if ((s = check_device(h))) return s;
+  SolveOpts so;
+  so.rtol = o->rtol;
+  so.atol = o->atol;
+  so.max_it = o->max_it;
+  so.flexible = o->flexible;
+  SolveResult r;
+  std::string err;
+  int rc = h->eng->pcg_solve(b, x, so, r, (cudaStream_t)stream, err);
+  if (rc) return fail((agg_status)rc, err);
+  if (res) {
+    res->iterations = r.iterations;
+    res->r0_norm = r.r0;
+    res->r_norm = r.rn;
+    res->status = r.status;
+  }
+  if (r.status) return fail((agg_status)r.status, agg_status_string(r.status));
+  return AGG_OK;
+}
+
+agg_status agg_operator_apply(agg_hier_t h, int level, const double* x, double* y, void* stream) {
+  if (!h || !x || !y) return fail(AGG_EINVAL, "NULL argument");
+  agg_status s = check_device(h);
+  if (s) return s;
+  std::string err;
+  int rc = h->eng->apply_level(level, x, y, (cudaStream_t)stream, err);
+  if (rc) return fail((agg_status)rc, err);
+  return AGG_OK;
+}
+
+agg_status agg_vcycle_apply(agg_hier_t h, const double* r, double* z, void* stream) {
+  if (!h || !r || !z) return fail(AGG_EINVAL, "NULL argument");
+  agg_status s = check_device(h);
+  if (s) return s;
+  std::string err;
+  int rc = h->eng->vcycle_apply(r, z, (cudaStream_t)stream, err);
+  if (rc) return fail((agg_status)rc, err);
+  return AGG_OK;
+}
+
+agg_status agg_ionic_update(const agg_ionic_params* p, double dt, int64_t n, const double* u, double* w,
+                            void* stream) {
+  if (!p || (n > 0 && (!u || !w))) return fail(AGG_EINVAL, "NULL argument");
+  if (n < 0) return fail(AGG_EINVAL, "n < 0");
+  if (p->model != AGG_FHN && p->model != AGG_ALIEV_PANFILOV) return fail(AGG_EINVAL, "ionic model");
+  if (n == 0) return AGG_OK;
+  IonicParams ip{p->model, p->k, p->a, p->eps, p->gamma, p->mu1, p->mu2};
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
+  k_ionic_update<<<blocks, 256, 0, (cudaStream_t)stream>>>(ip, dt, n, u, w);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(AGG_ECUDA, cudaGetErrorString(e));
+  return AGG_OK;
+}
+
+agg_status agg_monodomain_create(agg_hier_t h, const agg_sim_opts* o, agg_sim_t* out) {
+  if (!h || !o || !out) return fail(AGG_EINVAL, "NULL argument");
+  if (h->sim_active) return fail(AGG_EINVAL, "the hierarchy already drives a simulation");
+  agg_status s = check_pcg_opts(&o->pcg);
+  if (s) return s;
+  if ((s = check_device(h))) return s;
+  if (!(o->dt > 0) || !(o->chi_m > 0) || !(o->c_m > 0)) return fail(AGG_EINVAL, "dt, chi_m, c_m must be > 0");
+  const double c = o->chi_m * o->c_m / o->dt;
+  if (std::fabs(c - h->mass_coeff) > 1e-12 * std::fabs(c))
+    return fail(AGG_EINVAL, "hierarchy mass_coeff differs from chi_m c_m / dt");
+  if (o->ionic.model != AGG_FHN && o->ionic.model != AGG_ALIEV_PANFILOV) return fail(AGG_EINVAL, "ionic model");
+  SimParams sp;
+  sp.model = o->ionic.model;
+  sp.k = o->ionic.k;
+  sp.a = o->ionic.a;
+  sp.eps = o->ionic.eps;
+  sp.gamma = o->ionic.gamma;
+  sp.mu1 = o->ionic.mu1;
+  sp.mu2 = o->ionic.mu2;
+  sp.dt = o->dt;
+  sp.chi = o->chi_m;
+  sp.cm = o->c_m;
+  sp.iapp_value = o->iapp_mask_dev ? o->iapp_value : 0.0;
+  sp.iapp_steps = o->iapp_steps;
+  sp.pcg.rtol = o->pcg.rtol;
+  sp.pcg.atol = o->pcg.atol;
+  sp.pcg.max_it = o->pcg.max_it;
+  sp.pcg.flexible = o->pcg.flexible;
+  std::string err;
+  int rc = h->eng->sim_create(sp, o->iapp_mask_dev, nullptr, err);
+  if (rc) return fail((agg_status)rc, err);
+  agg_sim* sim = new (std::nothrow) agg_sim();
+  if (!sim) return fail(AGG_ENOMEM, "host allocation failed");
+  sim->h = h;
+  h->sim_active = true;
+  *out = sim;
+  return AGG_OK;
+}
+
+agg_status agg_monodomain_step(agg_sim_t sim, int n_steps, double* u, double* w, int* iters, void* stream) {
+  if (!sim || !u || !w) return fail(AGG_EINVAL, "NULL argument");
+  if (n_steps < 0) return fail(AGG_EINVAL, "n_steps < 0");
+  agg_status s = check_device(sim->h);
+  if (s) return s;
+  if (n_steps == 0) return AGG_OK;
+  std::string err;
+  int rc = sim->h->eng->sim_step(n_steps, u, w, iters, sim->clock, (cudaStream_t)stream, err);
+  if (rc) return fail((agg_status)rc, err.empty() ? agg_status_string(rc) : err);
+  return AGG_OK;
+}
+
+agg_status agg_profile_kernel(agg_hier_t h, int kernel, int reps, void* stream) {
+  if (!h || reps < 0) return fail(AGG_EINVAL, "bad argument");
+  agg_status s = check_device(h);
+  if (s) return s;
+  std::string err;
+  int rc = h->eng->kernel_loop(kernel, reps, (cudaStream_t)stream, err);
+  if (rc) return fail((agg_status)rc, err);
+  return AGG_OK;
+}
+
+agg_status agg_kernel_cost(agg_hier_t h, int kernel, double* bytes, double* flops) {
+  if (!h || !bytes || !flops) return fail(AGG_EINVAL, "NULL argument");
+  if (h->eng->kernel_cost(kernel, *bytes, *flops)) return fail(AGG_EINVAL, "unknown kernel id");
+  return AGG_OK;
+}
+
+agg_status agg_monodomain_set_clock(agg_sim_t sim, int64_t step) {
+  if (!sim || step < 0) return fail(AGG_EINVAL, "bad argument");
+  sim->clock = step;
+  return AGG_OK;
+}
+
+agg_status agg_monodomain_destroy(agg_sim_t sim) {
+  if (!sim) return AGG_OK;
+  sim->h->eng->sim_destroy();
+  sim->h->sim_active = false;
+  delete sim;
+  return AGG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,256 @@
+// Vector kernels of the outer float64 PCG recurrence (Section 6: CG
+// preconditioned by one V-cycle), the precision boundary, permutations and
+// the fused ionic update + right-hand side of the time step (Section 3.1).
+// Dot products are reduced deterministically: a fixed grid writes one partial
+// per block and the last block to finish sums them in block order.
+#pragma once
+#include "kernels.cuh"
+
+namespace aggmg {
+
+enum { TK_PQ = 0, TK_R = 1, TK_Z = 2, TK_R0 = 3 };
+
+__device__ __forceinline__ void finish_cond(CGState* st) { stop_loop(st); }
+
+// Reset of the per-solve fields; the options (rtol, atol, max_it, flexible,
+// cond, use_cond) are written by the host before the launch.
+static __global__ void k_cg_reset(CGState* st) {
+  st->guard = 0;
+  st->iter = 0;
+  st->done = 0;
+  st->status = 0;
+  st->rho = st->alpha = st->beta = st->pq = st->rr = st->r0 = 0.0;
+  st->rz_old = 0.0;
+}
+
+// Start of a solve: reset and select the WHILE node that this launch ends.
+static __global__ void k_cg_begin(CGState* st, unsigned long long cond, int use_cond) {
+  st->iter = 0;
+  st->done = 0;
+  st->status = 0;
+  st->rho = st->alpha = st->beta = st->pq = st->rr = st->r0 = 0.0;
+  st->rz_old = 0.0;
+  st->guard = 0;
+  st->cond = cond;
+  st->use_cond = use_cond;
+}
+
+static __global__ void k_set_opts(CGState* st, double rtol, double atol, int max_it, int flexible) {
+  st->rtol = rtol;
+  st->atol = atol;
+  st->max_it = max_it;
+  st->flexible = flexible;
+}
+
+static __global__ void k_noop() {}
+
+// ||r0||, tolerance, early exit when already converged
+static __global__ void __launch_bounds__(RED_NT) k_r0(const double* __restrict__ r, int64_t n, double* partials, CGState* st) {
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * RED_NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_NT)
+    s += r[i] * r[i];
+  if (partial_and_last<RED_NT>(s, partials, &st->ticket[TK_R0])) {
+    double rr = sum_partials<RED_NT>(partials, gridDim.x);
+    if (threadIdx.x == 0) {
+      st->ticket[TK_R0] = 0;
+      st->rr = rr;
+      st->r0 = sqrt(rr);
+      st->tol = fmax(st->rtol * st->r0, st->atol);
+      if (!isfinite(st->r0)) {
+        st->status = -6;
+        st->done = 1;
+        finish_cond(st);
+      } else if (st->r0 <= st->tol || st->r0 == 0.0) {
+        st->done = 1;
+        finish_cond(st);
+      }
+    }
+  }
+}
+
+// x += alpha p; r -= alpha q; ||r||; convergence test
+static __global__ void __launch_bounds__(RED_NT) k_cg_update(double* __restrict__ x, double* __restrict__ r,
+                                                      const double* __restrict__ p, const double* __restrict__ q,
+                                                      int64_t n, double* partials, CGState* st) {
+  if (st->done) return;
+  const double alpha = st->alpha;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * RED_NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_NT) {
+    x[i] += alpha * p[i];
+    double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    s += ri * ri;
+  }
+  if (partial_and_last<RED_NT>(s, partials, &st->ticket[TK_R])) {
+    double rr = sum_partials<RED_NT>(partials, gridDim.x);
+    if (threadIdx.x == 0) {
+      st->ticket[TK_R] = 0;
+      st->rr = rr;
+      st->iter += 1;
+      double rn = sqrt(rr);
+      if (!isfinite(rn)) {
+        st->status = -6;
+        st->done = 1;
+      } else if (rn <= st->tol) {
+        st->done = 1;
+      } else if (st->iter >= st->max_it) {
+        st->status = -5;
+        st->done = 1;
+      }
+      if (st->done) finish_cond(st);
+    }
+  }
+}
+
+// z64 <- zin (V-cycle output, any precision); rz = (r, z_new).
+// INIT: rho = rz.  Otherwise beta = rz / rho (Fletcher-Reeves form) or, for
+// the flexible variant, beta = (rz - (r, z_old)) / rho (Polak-Ribiere, with
+// (r, z_old) from k_flex_beta), then rho = rz.
+template <typename TZ, bool INIT>
+static __global__ void __launch_bounds__(RED_NT) k_zdot(const TZ* __restrict__ zin, double* __restrict__ z64,
+                                                 const double* __restrict__ r, int64_t n, double* partials,
+                                                 CGState* st) {
+  if (st->done) return;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * RED_NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_NT) {
+    const double zn = (double)zin[i];
+    z64[i] = zn;
+    s += r[i] * zn;
+  }
+  if (partial_and_last<RED_NT>(s, partials, &st->ticket[TK_Z])) {
+    const double rz = sum_partials<RED_NT>(partials, gridDim.x);
+    if (threadIdx.x == 0) {
+      st->ticket[TK_Z] = 0;
+      if (INIT) st->beta = 0.0;
+      else st->beta = (st->flexible ? rz - st->rz_old : rz) / st->rho;
+      st->rho = rz;
+    }
+  }
+}
+
+// Flexible (Polak-Ribiere) beta needs (r, z_old) of all blocks: done by a
+// separate pass so the partials of both sums are complete.
+static __global__ void __launch_bounds__(RED_NT) k_flex_beta(const double* __restrict__ r, const double* __restrict__ zold,
+                                                      int64_t n, double* partials, CGState* st) {
+  if (st->done || !st->flexible) return;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * RED_NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_NT)
+    s += r[i] * zold[i];
+  if (partial_and_last<RED_NT>(s, partials, &st->ticket[TK_PQ])) {
+    double so = sum_partials<RED_NT>(partials, gridDim.x);
+    if (threadIdx.x == 0) {
+      st->ticket[TK_PQ] = 0;
+      st->rz_old = so;
+    }
+  }
+}
+
+// p = z + beta p (INIT: p = z)
+template <bool INIT>
+static __global__ void __launch_bounds__(RED_NT) k_pupd(const double* __restrict__ z, double* __restrict__ p, int64_t n,
+                                                 const CGState* st) {
+  if (st->done) return;
+  const double beta = st->beta;
+  for (int64_t i = (int64_t)blockIdx.x * RED_NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_NT)
+    p[i] = INIT ? z[i] : z[i] + beta * p[i];
+}
+
+template <typename TO, typename TI>
+static __global__ void k_cast(const TI* __restrict__ in, TO* __restrict__ out, int64_t n, const CGState* st) {
+  if (st && st->done) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (TO)in[i];
+}
+
+// dst[i*B + r] = src[perm[i]*B + r]  (caller order -> internal order)
+template <typename TO, typename TI>
+static __global__ void k_gather_units(const TI* __restrict__ src, TO* __restrict__ dst, const int64_t* __restrict__ perm,
+                               int64_t n, int B) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= n * B) return;
+  const int64_t i = id / B;
+  const int r = (int)(id % B);
+  dst[id] = (TO)src[perm[i] * B + r];
+}
+// dst[perm[i]*B + r] = src[i*B + r]  (internal order -> caller order)
+template <typename TO, typename TI>
+static __global__ void k_scatter_units(const TI* __restrict__ src, TO* __restrict__ dst, const int64_t* __restrict__ perm,
+                                int64_t n, int B) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= n * B) return;
+  const int64_t i = id / B;
+  const int r = (int)(id % B);
+  dst[perm[i] * B + r] = (TO)src[id];
+}
+
+// ---------------------------------------------------------------- ionic models
+struct IonicParams {
+  int model;
+  double k, a, eps, gamma, mu1, mu2;
+};
+
+__device__ __forceinline__ void ionic_eval(const IonicParams& p, double u, double w, double& I, double& H) {
+  const double cub = p.k * u * (u - p.a) * (u - 1.0);
+  if (p.model == 0) {
+    I = cub + w;
+    H = p.eps * (u - p.gamma * w);
+  } else {
+    I = cub + u * w;
+    H = (p.eps + p.mu1 * w / (u + p.mu2)) * (-w - p.k * u * (u - p.a - 1.0));
+  }
+}
+
+static __global__ void k_ionic_update(IonicParams prm, double dt, int64_t n, const double* __restrict__ u,
+                               double* __restrict__ w) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double I, H;
+    ionic_eval(prm, u[i], w[i], I, H);
+    w[i] = w[i] + dt * H;
+  }
+}
+
+// Time step prologue for the thread's element (Section 3.1):
+//   w <- w + dt H(u, w);  f = I_app(t_{n+1}) mask - chi I(u, w_new);
+//   b_e = M_e (c u_e + f_e)   (ionic current interpolation)
+template <int B>
+static __global__ void __launch_bounds__(NT) k_ionic_rhs(const double* __restrict__ Me, const double* __restrict__ u,
+                                                  double* __restrict__ w, const double* __restrict__ mask,
+                                                  double* __restrict__ b, IonicParams prm, double dt, double chi,
+                                                  double c, double iapp_value, int64_t iapp_steps,
+                                                  const int64_t* __restrict__ step, int64_t nslices) {
+  constexpr int KP = Pad<double, B>::KP;
+  const int64_t unit = (int64_t)blockIdx.x * NT + threadIdx.x;
+  const int64_t slice = unit / SL;
+  const int lane = threadIdx.x & 31;
+  if (slice >= nslices) return;
+  const size_t o = (size_t)unit * B;
+  const double ia = (*step < iapp_steps) ? iapp_value : 0.0;
+  double t[B], acc[B];
+#pragma unroll
+  for (int r = 0; r < B; ++r) {
+    const double ur = u[o + r];
+    double I, H;
+    ionic_eval(prm, ur, w[o + r], I, H);
+    const double wn = w[o + r] + dt * H;
+    w[o + r] = wn;
+    ionic_eval(prm, ur, wn, I, H);
+    t[r] = c * ur + ia * mask[o + r] - chi * I;
+    acc[r] = 0.0;
+  }
+  block_mv<double, double, B>(Me + (size_t)slice * SL * KP, lane, t, acc);
+#pragma unroll
+  for (int r = 0; r < B; ++r) b[o + r] = acc[r];
+}
+
+// end of a time step: record the iteration count, advance the clock
+static __global__ void k_step_end(const CGState* st, int64_t* step, int* iters, int* slot, int capacity, int* status) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const int s = *slot;
+    if (s < capacity) iters[s] = st->iter;
+    if (st->status != 0 && *status == 0) *status = st->status;
+    *slot = s + 1;
+    *step = *step + 1;
+  }
+}
+
+}  // namespace aggmg

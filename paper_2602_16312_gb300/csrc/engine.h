@@ -1,0 +1,55 @@
+// Interface between the C ABI (capi.cu) and the per-block-size device
+// engines (engine_b*.cu). One engine owns the device copy of a hierarchy
+// and the CUDA graphs of the solver.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "setup.h"
+
+namespace aggmg {
+
+struct SolveOpts {
+  double rtol = 1e-8, atol = 0.0;
+  int max_it = 500, flexible = 0;
+};
+
+struct SolveResult {
+  int iterations = 0, status = 0;
+  double r0 = 0, rn = 0;
+};
+
+struct SimParams {
+  int model = 0;
+  double k = 0, a = 0, eps = 0, gamma = 0, mu1 = 0, mu2 = 0;
+  double dt = 0, chi = 1, cm = 1;
+  double iapp_value = 0;
+  int64_t iapp_steps = 0;
+  SolveOpts pcg;
+};
+
+class EngineBase {
+ public:
+  virtual ~EngineBase() {}
+  // upload the host hierarchy (and element mass blocks) and capture graphs
+  virtual int init(const HostHierarchy& h, const Mesh& m, int precision, cudaStream_t s, std::string& err) = 0;
+  virtual int pcg_solve(const double* b_user, double* x_user, const SolveOpts& o, SolveResult& res,
+                        cudaStream_t s, std::string& err) = 0;
+  virtual int apply_level(int level, const double* x_user, double* y_user, cudaStream_t s, std::string& err) = 0;
+  virtual int vcycle_apply(const double* r_user, double* z_user, cudaStream_t s, std::string& err) = 0;
+  // time stepping: one simulation per engine at a time
+  virtual int sim_create(const SimParams& p, const double* mask_user, cudaStream_t s, std::string& err) = 0;
+  virtual int sim_step(int n_steps, double* u_user, double* w_user, int* iters_host, int64_t& clock,
+                       cudaStream_t s, std::string& err) = 0;
+  virtual int sim_destroy() = 0;
+  virtual bool uses_conditional_graph() const = 0;
+  // instrumentation: launch one hot kernel `reps` times on the internal
+  // buffers, and its algorithmic bytes / flops per launch
+  virtual int kernel_loop(int id, int reps, cudaStream_t s, std::string& err) = 0;
+  virtual int kernel_cost(int id, double& bytes, double& flops) const = 0;
+};
+
+EngineBase* make_engine(int B, int precision);
+
+}  // namespace aggmg

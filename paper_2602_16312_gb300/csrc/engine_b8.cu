@@ -1,0 +1,13 @@
+// Engine instantiations for element blocks of B = 8 DoFs.
+#include "engine_impl.cuh"
+
+namespace aggmg {
+EngineBase* make_engine_b8(int precision) {
+  switch (precision) {
+    case AGG_F64: return new Engine<double, double, 8>();
+    case AGG_F32: return new Engine<float, float, 8>();
+    case AGG_F32_BF16SMOOTH: return new Engine<float, __nv_bfloat16, 8>();
+    default: return nullptr;
+  }
+}
+}  // namespace aggmg

@@ -1,0 +1,587 @@
+// Device engine for one block size B and one V-cycle precision:
+//   T  = float64 or float32 (V-cycle matrices and vectors),
+//   TD = storage type of the smoother block inverses (T or bfloat16).
+// The outer PCG (Section 6) is always float64 on the float64 fine operator.
+//
+// Solver graphs: the PCG set-up kernels, then a CUDA-graph WHILE node whose
+// body is one PCG iteration; the convergence test in k_cg_update ends the
+// loop on the device, so a whole solve (or time step) is one graph launch
+// with no host round trip. If the runtime refuses conditional nodes, the
+// engine falls back to launching the iteration graph in batches and polling
+// the device flag.
+#pragma once
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "../../include/aggmg.h"
+#include "cg_kernels.cuh"
+#include "engine.h"
+#include "kernels.cuh"
+
+namespace aggmg {
+
+#define AGG_CK(call)                                                              \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      err = std::string(#call) + " failed: " + cudaGetErrorString(e_);            \
+      return AGG_ECUDA;                                                           \
+    }                                                                             \
+  } while (0)
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+template <typename TS>
+inline TS to_storage(double v) {
+  return static_cast<TS>(v);
+}
+template <>
+inline __nv_bfloat16 to_storage<__nv_bfloat16>(double v) {
+  return __float2bfloat16_rn((float)v);
+}
+
+template <typename T, typename TD, int B>
+class Engine : public EngineBase {
+  struct Lev {
+    int64_t n = 0, nsl = 0, nvec = 0;
+    int32_t* slice_ptr = nullptr;
+    int32_t* cols = nullptr;
+    T* vals = nullptr;
+    TD* Dinv = nullptr;
+    T* P = nullptr;
+    int32_t* parent = nullptr;
+    int64_t* child_ptr = nullptr;
+    int64_t* perm = nullptr;
+    T *xa = nullptr, *xb = nullptr, *d = nullptr, *rhs = nullptr, *S = nullptr;
+    std::vector<T> c1, c2;
+    SellView<T> A() const { return SellView<T>{slice_ptr, cols, vals, nsl}; }
+  };
+
+  std::vector<Lev> lev_;
+  std::vector<int64_t> nnzb_;
+  int nlev_ = 0, degree_ = 3;
+  SellView<double> A0_{};
+  double* Me_ = nullptr;
+  double *Linv_ = nullptr, *U_ = nullptr, *yc_ = nullptr;
+  int64_t nc_ = 0;
+  double *b_ = nullptr, *x_ = nullptr, *r_ = nullptr, *p_ = nullptr, *q_ = nullptr, *z_ = nullptr;
+  double* partials_ = nullptr;
+  float* r32_ = nullptr;
+  CGState* st_ = nullptr;
+  CGState* st_host_ = nullptr;
+  std::vector<void*> allocs_;
+  cudaStream_t cs_ = nullptr;
+  bool use_cond_ = false;
+  // solve graphs
+  cudaGraphExec_t solve_exec_ = nullptr, init_exec_ = nullptr, body_exec_ = nullptr;
+  std::vector<cudaGraph_t> graphs_;
+  // simulation
+  bool sim_ = false;
+  SimParams sp_{};
+  double *w_ = nullptr, *mask_ = nullptr;
+  int64_t* step_ = nullptr;
+  int *iters_ = nullptr, *slot_ = nullptr, *sim_status_ = nullptr;
+  int cap_ = 1024;
+  cudaGraphExec_t step_exec_ = nullptr, step_pro_exec_ = nullptr, step_epi_exec_ = nullptr;
+
+  template <typename X>
+  int dalloc(X** p, size_t count, std::string& err) {
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, std::max<size_t>(count, 1) * sizeof(X));
+    if (e != cudaSuccess) {
+      err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+      return AGG_ENOMEM;
+    }
+    cudaMemset(v, 0, std::max<size_t>(count, 1) * sizeof(X));
+    allocs_.push_back(v);
+    *p = static_cast<X*>(v);
+    return AGG_OK;
+  }
+  template <typename X>
+  int upload(X** p, const X* host, size_t count, std::string& err) {
+    int s = dalloc(p, count, err);
+    if (s) return s;
+    AGG_CK(cudaMemcpy(*p, host, count * sizeof(X), cudaMemcpyHostToDevice));
+    return AGG_OK;
+  }
+
+  // pack B x B row-major blocks into the sliced layout [k/VW][lane][k%VW], k = c*B + r
+  template <typename TS>
+  static void pack(const double* blk, TS* slot_base, int lane) {
+    constexpr int VW = Vec<TS>::W;
+    for (int k = 0; k < B * B; ++k) {
+      const int c = k / B, r = k % B;
+      slot_base[((size_t)(k / VW) * SL + lane) * VW + (k % VW)] = to_storage<TS>(blk[r * B + c]);
+    }
+  }
+
+  template <typename TS>
+  int upload_sell(const BlockCSR& A, int64_t nsl, int32_t** sp, int32_t** cols, TS** vals, std::string& err) {
+    constexpr int KP = Pad<TS, B>::KP;
+    const int64_t n = A.nrows;
+    std::vector<int32_t> hsp(nsl + 1, 0);
+    for (int64_t s = 0; s < nsl; ++s) {
+      int64_t mx = 1;
+      for (int64_t u = s * SL; u < std::min<int64_t>(n, (s + 1) * SL); ++u)
+        mx = std::max<int64_t>(mx, A.rowptr[u + 1] - A.rowptr[u]);
+      hsp[s + 1] = hsp[s] + (int32_t)mx;
+    }
+    const int64_t nslots = hsp[nsl];
+    std::vector<int32_t> hc((size_t)nslots * SL, 0);
+    std::vector<TS> hv((size_t)nslots * SL * KP, to_storage<TS>(0.0));
+    for (int64_t s = 0; s < nsl; ++s)
+      for (int lane = 0; lane < SL; ++lane) {
+        const int64_t u = s * SL + lane;
+        const int64_t len = (u < n) ? A.rowptr[u + 1] - A.rowptr[u] : 0;
+        for (int64_t j = 0; j < hsp[s + 1] - hsp[s]; ++j) {
+          const int64_t slot = hsp[s] + j;
+          if (j < len) {
+            const int64_t k = A.rowptr[u] + j;
+            hc[slot * SL + lane] = A.col[k];
+            pack<TS>(&A.val[(size_t)k * B * B], &hv[(size_t)slot * SL * KP], lane);
+          } else {
+            hc[slot * SL + lane] = (int32_t)(u < n ? u : 0);
+          }
+        }
+      }
+    int s = upload(sp, hsp.data(), hsp.size(), err);
+    if (!s) s = upload(cols, hc.data(), hc.size(), err);
+    if (!s) s = upload(vals, hv.data(), hv.size(), err);
+    return s;
+  }
+
+  template <typename TS>
+  int upload_blocks(const std::vector<double>& blocks, int64_t n, int64_t nsl, TS** out, std::string& err) {
+    constexpr int KP = Pad<TS, B>::KP;
+    std::vector<TS> hv((size_t)nsl * SL * KP, to_storage<TS>(0.0));
+    for (int64_t u = 0; u < n; ++u)
+      pack<TS>(&blocks[(size_t)u * B * B], &hv[(size_t)(u / SL) * SL * KP], (int)(u % SL));
+    return upload(out, hv.data(), hv.size(), err);
+  }
+
+  // ---------------------------------------------------------------- V-cycle
+  // Launches one V-cycle from level l (rhs in lev_[l].rhs); returns the buffer
+  // holding the correction.
+  T* vc(int l, cudaStream_t s) {
+    Lev& v = lev_[l];
+    if (l == nlev_ - 1) {
+      const int64_t g = cdiv(nc_ * 32, 256);
+      k_coarse_lower<T><<<g, 256, 0, s>>>(Linv_, v.rhs, yc_, nc_, st_);
+      k_coarse_upper<T><<<g, 256, 0, s>>>(U_, yc_, v.xa, nc_, st_);
+      return v.xa;
+    }
+    const int64_t g = cdiv(v.nsl * SL, NT);
+    T* xo = v.xa;
+    T* xn = v.xb;
+    const SellView<T> A = v.A();
+    k_cheb<T, TD, B, 0><<<g, NT, 0, s>>>(A, v.Dinv, v.rhs, nullptr, xo, v.d, T(0), v.c2[0], v.nsl, st_);
+    for (int k = 1; k < degree_; ++k) {
+      k_cheb<T, TD, B, 2><<<g, NT, 0, s>>>(A, v.Dinv, v.rhs, xo, xn, v.d, v.c1[k], v.c2[k], v.nsl, st_);
+      std::swap(xo, xn);
+    }
+    Lev& c = lev_[l + 1];
+    k_resid_restrict<T, B><<<g, NT, 0, s>>>(A, v.P, v.rhs, xo, v.S, st_);
+    k_segsum<T, B><<<cdiv(c.n * B, 256), 256, 0, s>>>(c.child_ptr, v.S, c.rhs, c.n, st_);
+    T* ec = vc(l + 1, s);
+    k_prolong<T, B><<<g, NT, 0, s>>>(v.P, v.parent, ec, xo, v.nsl, st_);
+    k_cheb<T, TD, B, 1><<<g, NT, 0, s>>>(A, v.Dinv, v.rhs, xo, xn, v.d, T(0), v.c2[0], v.nsl, st_);
+    std::swap(xo, xn);
+    for (int k = 1; k < degree_; ++k) {
+      k_cheb<T, TD, B, 2><<<g, NT, 0, s>>>(A, v.Dinv, v.rhs, xo, xn, v.d, v.c1[k], v.c2[k], v.nsl, st_);
+      std::swap(xo, xn);
+    }
+    return xo;
+  }
+
+  int64_t N0() const { return lev_[0].nvec; }
+  int64_t g0() const { return cdiv(lev_[0].nsl * SL, NT); }
+
+  void launch_precond(cudaStream_t s, bool init) {
+    const int64_t N = N0();
+    if (!std::is_same<T, double>::value)
+      k_cast<float, double><<<RED_BLOCKS, RED_NT, 0, s>>>(r_, r32_, N, st_);
+    T* out = vc(0, s);
+    if (init) {
+      k_zdot<T, true><<<RED_BLOCKS, RED_NT, 0, s>>>(out, z_, r_, N, partials_, st_);
+      k_pupd<true><<<RED_BLOCKS, RED_NT, 0, s>>>(z_, p_, N, st_);
+    } else {
+      k_flex_beta<<<RED_BLOCKS, RED_NT, 0, s>>>(r_, z_, N, partials_, st_);
+      k_zdot<T, false><<<RED_BLOCKS, RED_NT, 0, s>>>(out, z_, r_, N, partials_, st_);
+      k_pupd<false><<<RED_BLOCKS, RED_NT, 0, s>>>(z_, p_, N, st_);
+    }
+  }
+
+  void launch_init(cudaStream_t s, unsigned long long cond, int use_cond) {
+    k_cg_begin<<<1, 1, 0, s>>>(st_, cond, use_cond);
+    k_spmv<double, B, 1><<<g0(), NT, 0, s>>>(A0_, x_, b_, r_, nullptr, nullptr);
+    k_r0<<<RED_BLOCKS, RED_NT, 0, s>>>(r_, N0(), partials_, st_);
+    launch_precond(s, true);
+  }
+
+  void launch_body(cudaStream_t s) {
+    k_spmv<double, B, 2><<<g0(), NT, 0, s>>>(A0_, p_, nullptr, q_, partials_, st_);
+    k_cg_update<<<RED_BLOCKS, RED_NT, 0, s>>>(x_, r_, p_, q_, N0(), partials_, st_);
+    launch_precond(s, false);
+  }
+
+  void launch_step_prologue(cudaStream_t s) {
+    IonicParams ip{sp_.model, sp_.k, sp_.a, sp_.eps, sp_.gamma, sp_.mu1, sp_.mu2};
+    const double c = sp_.chi * sp_.cm / sp_.dt;
+    k_ionic_rhs<B><<<g0(), NT, 0, s>>>(Me_, x_, w_, mask_, b_, ip, sp_.dt, sp_.chi, c, sp_.iapp_value,
+                                       sp_.iapp_steps, step_, lev_[0].nsl);
+  }
+
+  // Builds [prologue] -> WHILE(body) -> [epilogue]; prologue/epilogue are
+  // callables launching kernels on a capture stream.
+  template <typename Pro, typename Epi>
+  int build_cond_graph(Pro pro, Epi epi, cudaGraphExec_t* exec, std::string& err) {
+    cudaGraph_t g;
+    AGG_CK(cudaGraphCreate(&g, 0));
+    graphs_.push_back(g);
+    cudaGraphConditionalHandle h;
+    AGG_CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraph_t gp, ge;
+    AGG_CK(cudaStreamBeginCapture(cs_, cudaStreamCaptureModeThreadLocal));
+    pro(cs_, (unsigned long long)h, 1);
+    AGG_CK(cudaStreamEndCapture(cs_, &gp));
+    graphs_.push_back(gp);
+    cudaGraphNode_t n0, n1, n2;
+    AGG_CK(cudaGraphAddChildGraphNode(&n0, g, nullptr, 0, gp));
+    // zero-initialised parameter block (the union has no usable default constructor)
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+    std::memset(raw, 0, sizeof(raw));
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    AGG_CK(cudaGraphAddNode(&n1, g, &n0, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    AGG_CK(cudaStreamBeginCaptureToGraph(cs_, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    launch_body(cs_);
+    AGG_CK(cudaStreamEndCapture(cs_, &body));
+    AGG_CK(cudaStreamBeginCapture(cs_, cudaStreamCaptureModeThreadLocal));
+    epi(cs_);
+    AGG_CK(cudaStreamEndCapture(cs_, &ge));
+    graphs_.push_back(ge);
+    AGG_CK(cudaGraphAddChildGraphNode(&n2, g, &n1, 1, ge));
+    AGG_CK(cudaGraphInstantiate(exec, g, 0));
+    return AGG_OK;
+  }
+
+  template <typename F>
+  int capture(F f, cudaGraphExec_t* exec, std::string& err) {
+    cudaGraph_t g;
+    AGG_CK(cudaStreamBeginCapture(cs_, cudaStreamCaptureModeThreadLocal));
+    f(cs_);
+    AGG_CK(cudaStreamEndCapture(cs_, &g));
+    graphs_.push_back(g);
+    AGG_CK(cudaGraphInstantiate(exec, g, 0));
+    return AGG_OK;
+  }
+
+  // run a prepared solve on the internal buffers; batch fallback polls `done`
+  int run_solve(cudaGraphExec_t cond_exec, cudaGraphExec_t pro, cudaGraphExec_t epi, cudaStream_t s,
+                std::string& err) {
+    if (use_cond_) {
+      AGG_CK(cudaGraphLaunch(cond_exec, s));
+      return AGG_OK;
+    }
+    AGG_CK(cudaGraphLaunch(pro, s));
+    int launched = 0;
+    int batch = 4;
+    for (;;) {
+      for (int i = 0; i < batch; ++i) AGG_CK(cudaGraphLaunch(body_exec_, s));
+      launched += batch;
+      AGG_CK(cudaMemcpyAsync(st_host_, st_, sizeof(CGState), cudaMemcpyDeviceToHost, s));
+      AGG_CK(cudaStreamSynchronize(s));
+      if (st_host_->done || launched > st_host_->max_it + 1) break;
+      batch = std::min(2 * batch, 64);
+    }
+    if (epi) AGG_CK(cudaGraphLaunch(epi, s));
+    return AGG_OK;
+  }
+
+ public:
+  ~Engine() override {
+    if (cs_) cudaStreamSynchronize(cs_);
+    for (auto e : {solve_exec_, init_exec_, body_exec_, step_exec_, step_pro_exec_, step_epi_exec_})
+      if (e) cudaGraphExecDestroy(e);
+    for (auto g : graphs_) cudaGraphDestroy(g);
+    for (void* p : allocs_) cudaFree(p);
+    if (st_host_) cudaFreeHost(st_host_);
+    if (cs_) cudaStreamDestroy(cs_);
+  }
+
+  bool uses_conditional_graph() const override { return use_cond_; }
+
+  int init(const HostHierarchy& h, const Mesh& m, int precision, cudaStream_t s, std::string& err) override {
+    (void)precision;
+    nlev_ = h.L;
+    degree_ = 3;
+    lev_.assign(nlev_, Lev());
+    AGG_CK(cudaStreamCreateWithFlags(&cs_, cudaStreamNonBlocking));
+    AGG_CK(cudaMallocHost(&st_host_, sizeof(CGState)));
+    std::memset(st_host_, 0, sizeof(CGState));
+    int rc;
+    if ((rc = dalloc(&st_, 1, err))) return rc;
+    for (int l = 0; l < nlev_; ++l) nnzb_.push_back(h.lev[l].A.nnzb());
+    for (int l = 0; l < nlev_; ++l) {
+      const HostLevel& hl = h.lev[l];
+      Lev& v = lev_[l];
+      v.n = hl.n;
+      v.nsl = cdiv(hl.n, SL);
+      v.nvec = v.nsl * SL * B;
+      if ((rc = upload(&v.perm, hl.perm.data(), hl.perm.size(), err))) return rc;
+      const bool coarsest = (l == nlev_ - 1);
+      if (!coarsest) {
+        if ((rc = upload_sell<T>(hl.A, v.nsl, &v.slice_ptr, &v.cols, &v.vals, err))) return rc;
+        if ((rc = upload_blocks<TD>(hl.Dinv, hl.n, v.nsl, &v.Dinv, err))) return rc;
+        if ((rc = upload_blocks<T>(hl.P, hl.n, v.nsl, &v.P, err))) return rc;
+        std::vector<int32_t> par(v.nsl * SL, 0);
+        std::copy(hl.parent.begin(), hl.parent.end(), par.begin());
+        if ((rc = upload(&v.parent, par.data(), par.size(), err))) return rc;
+        // Chebyshev coefficients (recurrence of O10)
+        const double th = 0.5 * (hl.lam_max + hl.lam_min), de = 0.5 * (hl.lam_max - hl.lam_min);
+        const double sig = th / de;
+        double rho = 1.0 / sig;
+        v.c1.assign(degree_, T(0));
+        v.c2.assign(degree_, T(0));
+        v.c2[0] = T(1.0 / th);
+        for (int k = 1; k < degree_; ++k) {
+          const double rn = 1.0 / (2.0 * sig - rho);
+          v.c1[k] = T(rn * rho);
+          v.c2[k] = T(2.0 * rn / de);
+          rho = rn;
+        }
+        if ((rc = dalloc(&v.xb, v.nvec, err))) return rc;
+        if ((rc = dalloc(&v.d, v.nvec, err))) return rc;
+        if ((rc = dalloc(&v.S, v.nvec, err))) return rc;
+      }
+      if (l > 0) {
+        if ((rc = upload(&v.child_ptr, hl.child_ptr.data(), hl.child_ptr.size(), err))) return rc;
+        if ((rc = dalloc(&v.rhs, v.nvec, err))) return rc;
+      }
+      if ((rc = dalloc(&v.xa, v.nvec, err))) return rc;
+    }
+    // float64 fine operator of the outer CG
+    if (std::is_same<T, double>::value && nlev_ > 1) {
+      A0_ = SellView<double>{lev_[0].slice_ptr, lev_[0].cols, reinterpret_cast<double*>(lev_[0].vals), lev_[0].nsl};
+    } else {
+      int32_t *sp, *cols;
+      double* vals;
+      if ((rc = upload_sell<double>(h.lev[0].A, lev_[0].nsl, &sp, &cols, &vals, err))) return rc;
+      A0_ = SellView<double>{sp, cols, vals, lev_[0].nsl};
+    }
+    // element mass blocks in internal order for the right-hand side
+    {
+      std::vector<double> me((size_t)m.ne * B * B);
+      for (int64_t r = 0; r < m.ne; ++r)
+        std::memcpy(&me[(size_t)r * B * B], &m.Me[(size_t)h.lev[0].perm[r] * B * B], sizeof(double) * B * B);
+      if ((rc = upload_blocks<double>(me, m.ne, lev_[0].nsl, &Me_, err))) return rc;
+    }
+    // coarsest: inverse Cholesky factor and its transpose
+    nc_ = h.nc;
+    {
+      std::vector<double> Ut((size_t)nc_ * nc_);
+      for (int64_t i = 0; i < nc_; ++i)
+        for (int64_t j = 0; j < nc_; ++j) Ut[(size_t)j * nc_ + i] = h.Linv[(size_t)i * nc_ + j];
+      if ((rc = upload(&Linv_, h.Linv.data(), h.Linv.size(), err))) return rc;
+      if ((rc = upload(&U_, Ut.data(), Ut.size(), err))) return rc;
+      if ((rc = dalloc(&yc_, nc_, err))) return rc;
+    }
+    const int64_t N = N0();
+    for (double** pp : {&b_, &x_, &r_, &p_, &q_, &z_})
+      if ((rc = dalloc(pp, N, err))) return rc;
+    if (!std::is_same<T, double>::value)
+      if ((rc = dalloc(&r32_, N, err))) return rc;
+    const int64_t nparts = std::max<int64_t>(2 * RED_BLOCKS, 2 * g0() + 64);
+    if ((rc = dalloc(&partials_, nparts, err))) return rc;
+    lev_[0].rhs = std::is_same<T, double>::value ? reinterpret_cast<T*>(r_) : reinterpret_cast<T*>(r32_);
+    AGG_CK(cudaDeviceSynchronize());
+    // graphs: conditional WHILE solve, with the batch fallback prepared as well
+    if ((rc = capture([&](cudaStream_t c) { launch_init(c, 0, 0); }, &init_exec_, err))) return rc;
+    if ((rc = capture([&](cudaStream_t c) { launch_body(c); }, &body_exec_, err))) return rc;
+    std::string cerr;
+    use_cond_ = build_cond_graph([&](cudaStream_t c, unsigned long long hd, int u) { launch_init(c, hd, u); },
+                                 [&](cudaStream_t c) { k_noop<<<1, 1, 0, c>>>(); }, &solve_exec_, cerr) == AGG_OK;
+    if (!use_cond_) {
+      cudaGetLastError();
+      cudaStreamCaptureStatus cst;
+      if (cudaStreamIsCapturing(cs_, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+        cudaGraph_t dummy = nullptr;
+        cudaStreamEndCapture(cs_, &dummy);
+        if (dummy) cudaGraphDestroy(dummy);
+      }
+      cudaGetLastError();
+    }
+    if (getenv("AGG_NO_COND_GRAPH")) use_cond_ = false;
+    (void)s;
+    return AGG_OK;
+  }
+
+  int pcg_solve(const double* b_user, double* x_user, const SolveOpts& o, SolveResult& res, cudaStream_t s,
+                std::string& err) override {
+    const Lev& v0 = lev_[0];
+    const int64_t ne = v0.n;
+    const int64_t g = cdiv(ne * B, 256);
+    k_gather_units<double, double><<<g, 256, 0, s>>>(b_user, b_, v0.perm, ne, B);
+    k_gather_units<double, double><<<g, 256, 0, s>>>(x_user, x_, v0.perm, ne, B);
+    k_set_opts<<<1, 1, 0, s>>>(st_, o.rtol, o.atol, o.max_it, o.flexible);
+    int rc = run_solve(solve_exec_, init_exec_, nullptr, s, err);
+    if (rc) return rc;
+    k_scatter_units<double, double><<<g, 256, 0, s>>>(x_, x_user, v0.perm, ne, B);
+    AGG_CK(cudaMemcpyAsync(st_host_, st_, sizeof(CGState), cudaMemcpyDeviceToHost, s));
+    AGG_CK(cudaStreamSynchronize(s));
+    AGG_CK(cudaGetLastError());
+    res.iterations = st_host_->iter;
+    res.r0 = st_host_->r0;
+    res.rn = std::sqrt(st_host_->rr);
+    res.status = st_host_->status;
+    return AGG_OK;
+  }
+
+  int apply_level(int l, const double* x_user, double* y_user, cudaStream_t s, std::string& err) override {
+    if (l < 0 || l >= nlev_) { err = "level out of range"; return AGG_EINVAL; }
+    Lev& v = lev_[l];
+    const int64_t g = cdiv(v.n * B, 256);
+    if (l == 0) {
+      k_gather_units<double, double><<<g, 256, 0, s>>>(x_user, p_, v.perm, v.n, B);
+      k_spmv<double, B, 0><<<g0(), NT, 0, s>>>(A0_, p_, nullptr, q_, nullptr, nullptr);
+      k_scatter_units<double, double><<<g, 256, 0, s>>>(q_, y_user, v.perm, v.n, B);
+    } else {
+      if (l == nlev_ - 1) { err = "the coarsest level is applied through its Cholesky factor only"; return AGG_EUNSUPPORTED; }
+      k_gather_units<T, double><<<g, 256, 0, s>>>(x_user, v.xa, v.perm, v.n, B);
+      k_spmv<T, B, 0><<<cdiv(v.nsl * SL, NT), NT, 0, s>>>(v.A(), v.xa, nullptr, v.xb, nullptr, nullptr);
+      k_scatter_units<double, T><<<g, 256, 0, s>>>(v.xb, y_user, v.perm, v.n, B);
+    }
+    AGG_CK(cudaGetLastError());
+    return AGG_OK;
+  }
+
+  int vcycle_apply(const double* r_user, double* z_user, cudaStream_t s, std::string& err) override {
+    Lev& v = lev_[0];
+    const int64_t g = cdiv(v.n * B, 256);
+    k_cg_reset<<<1, 1, 0, s>>>(st_);
+    k_gather_units<double, double><<<g, 256, 0, s>>>(r_user, r_, v.perm, v.n, B);
+    if (!std::is_same<T, double>::value)
+      k_cast<float, double><<<RED_BLOCKS, RED_NT, 0, s>>>(r_, r32_, N0(), st_);
+    T* out = vc(0, s);
+    k_scatter_units<double, T><<<g, 256, 0, s>>>(out, z_user, v.perm, v.n, B);
+    AGG_CK(cudaGetLastError());
+    return AGG_OK;
+  }
+
+  int sim_create(const SimParams& p, const double* mask_user, cudaStream_t s, std::string& err) override {
+    if (sim_) { err = "a simulation already uses this hierarchy"; return AGG_EINVAL; }
+    sp_ = p;
+    int rc;
+    const int64_t N = N0();
+    if (!w_) {
+      if ((rc = dalloc(&w_, N, err))) return rc;
+      if ((rc = dalloc(&mask_, N, err))) return rc;
+      if ((rc = dalloc(&step_, 1, err))) return rc;
+      if ((rc = dalloc(&iters_, cap_, err))) return rc;
+      if ((rc = dalloc(&slot_, 1, err))) return rc;
+      if ((rc = dalloc(&sim_status_, 1, err))) return rc;
+    }
+    const Lev& v0 = lev_[0];
+    if (mask_user)
+      k_gather_units<double, double><<<cdiv(v0.n * B, 256), 256, 0, s>>>(mask_user, mask_, v0.perm, v0.n, B);
+    AGG_CK(cudaMemsetAsync(step_, 0, sizeof(int64_t), s));
+    AGG_CK(cudaStreamSynchronize(s));
+    if (step_exec_) { cudaGraphExecDestroy(step_exec_); step_exec_ = nullptr; }
+    if (step_pro_exec_) { cudaGraphExecDestroy(step_pro_exec_); step_pro_exec_ = nullptr; }
+    if (step_epi_exec_) { cudaGraphExecDestroy(step_epi_exec_); step_epi_exec_ = nullptr; }
+    auto pro = [&](cudaStream_t c, unsigned long long hd, int u) {
+      launch_step_prologue(c);
+      launch_init(c, hd, u);
+    };
+    auto epi = [&](cudaStream_t c) { k_step_end<<<1, 1, 0, c>>>(st_, step_, iters_, slot_, cap_, sim_status_); };
+    if (use_cond_) {
+      if ((rc = build_cond_graph(pro, epi, &step_exec_, err))) return rc;
+    } else {
+      if ((rc = capture([&](cudaStream_t c) { pro(c, 0, 0); }, &step_pro_exec_, err))) return rc;
+      if ((rc = capture(epi, &step_epi_exec_, err))) return rc;
+    }
+    sim_ = true;
+    return AGG_OK;
+  }
+
+  int sim_step(int n_steps, double* u_user, double* w_user, int* iters_host, int64_t& clock, cudaStream_t s,
+               std::string& err) override {
+    if (!sim_) { err = "no simulation"; return AGG_EINVAL; }
+    const Lev& v0 = lev_[0];
+    const int64_t g = cdiv(v0.n * B, 256);
+    k_gather_units<double, double><<<g, 256, 0, s>>>(u_user, x_, v0.perm, v0.n, B);
+    k_gather_units<double, double><<<g, 256, 0, s>>>(w_user, w_, v0.perm, v0.n, B);
+    AGG_CK(cudaMemcpyAsync(step_, &clock, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    AGG_CK(cudaMemsetAsync(sim_status_, 0, sizeof(int), s));
+    k_set_opts<<<1, 1, 0, s>>>(st_, sp_.pcg.rtol, sp_.pcg.atol, sp_.pcg.max_it, sp_.pcg.flexible);
+    int done = 0;
+    int status = 0;
+    std::vector<int> its;
+    while (done < n_steps) {
+      const int chunk = std::min(cap_, n_steps - done);
+      AGG_CK(cudaMemsetAsync(slot_, 0, sizeof(int), s));
+      for (int i = 0; i < chunk; ++i) {
+        int rc = run_solve(step_exec_, step_pro_exec_, step_epi_exec_, s, err);
+        if (rc) return rc;
+      }
+      if (iters_host) {
+        its.resize(chunk);
+        AGG_CK(cudaMemcpyAsync(its.data(), iters_, sizeof(int) * chunk, cudaMemcpyDeviceToHost, s));
+        AGG_CK(cudaStreamSynchronize(s));
+        std::copy(its.begin(), its.end(), iters_host + done);
+      }
+      done += chunk;
+    }
+    k_scatter_units<double, double><<<g, 256, 0, s>>>(x_, u_user, v0.perm, v0.n, B);
+    k_scatter_units<double, double><<<g, 256, 0, s>>>(w_, w_user, v0.perm, v0.n, B);
+    AGG_CK(cudaMemcpyAsync(&status, sim_status_, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AGG_CK(cudaStreamSynchronize(s));
+    AGG_CK(cudaGetLastError());
+    clock += n_steps;
+    return status;
+  }
+
+  int kernel_loop(int id, int reps, cudaStream_t s, std::string& err) override {
+    Lev& v = lev_[0];
+    const int64_t g = g0();
+    for (int i = 0; i < reps; ++i) {
+      switch (id) {
+        case 0: k_spmv<double, B, 0><<<g, NT, 0, s>>>(A0_, p_, nullptr, q_, nullptr, nullptr); break;
+        case 1:
+          k_cheb<T, TD, B, 2><<<g, NT, 0, s>>>(v.A(), v.Dinv, v.rhs, v.xa, v.xb, v.d, v.c1[1], v.c2[1], v.nsl, nullptr);
+          break;
+        case 2: k_resid_restrict<T, B><<<g, NT, 0, s>>>(v.A(), v.P, v.rhs, v.xa, v.S, nullptr); break;
+        case 3: k_prolong<T, B><<<g, NT, 0, s>>>(v.P, v.parent, lev_[1].xa, v.xb, v.nsl, nullptr); break;
+        default: err = "unknown kernel id"; return AGG_EINVAL;
+      }
+    }
+    AGG_CK(cudaGetLastError());
+    return AGG_OK;
+  }
+
+  int kernel_cost(int id, double& bytes, double& flops) const override {
+    const double n0 = (double)lev_[0].n, N = n0 * B, nz = (double)nnzb_[0], bb = (double)B * B;
+    const double sT = sizeof(T), sD = sizeof(TD);
+    switch (id) {
+      case 0: bytes = nz * (bb * 8 + 4) + 2 * N * 8; flops = 2 * nz * bb; break;
+      case 1: bytes = nz * (bb * sT + 4) + n0 * bb * sD + 5 * N * sT; flops = 2 * nz * bb + 2 * n0 * bb + 4 * N; break;
+      case 2: bytes = nz * (bb * sT + 4) + n0 * bb * sT + 3 * N * sT; flops = 2 * nz * bb + 2 * n0 * bb + N; break;
+      case 3: bytes = n0 * bb * sT + 2 * N * sT + (double)lev_[1].n * B * sT + n0 * 4; flops = 2 * n0 * bb + N; break;
+      default: return AGG_EINVAL;
+    }
+    return AGG_OK;
+  }
+
+  int sim_destroy() override {
+    sim_ = false;
+    return AGG_OK;
+  }
+};
+
+}  // namespace aggmg

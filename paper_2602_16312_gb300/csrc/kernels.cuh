@@ -1,0 +1,377 @@
+// Device kernels of the per-step hot path (sm_103a).
+//
+// Data layout ("sliced blocks"): units (elements on level 0, agglomerates on
+// coarser levels) are grouped in slices of 32; one thread owns one unit and
+// computes its B = (p+1)^d outputs in registers. A B x B block of every unit
+// of a slice is stored as KP = B*B (rounded up to 16 bytes) values in the
+// order [k / VW][lane][k % VW] with k = c*B + r (c column, r row) and
+// VW = 16 / sizeof(T): a warp reads 512 contiguous bytes per vector load.
+// Block-sparse operators store one such slot per (slice, neighbour slot)
+// plus a column index per (slot, lane); rows with fewer blocks than the
+// slice maximum are padded with zero blocks pointing at the row itself.
+// Vectors are unit-major: entry u*B + i.
+//
+// Every kernel of a PCG iteration reads the solver's `done` flag first and
+// returns at once when the iteration has converged, so extra launches after
+// convergence do no work.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace aggmg {
+
+constexpr int SL = 32;          // units per slice
+constexpr int NT = 128;         // threads per block for unit kernels
+constexpr int RED_BLOCKS = 1216; // fixed grid of the reduction kernels (152 SMs x 8)
+constexpr int RED_NT = 256;
+
+// ---------------------------------------------------------------- PCG state
+struct CGState {
+  double rho, alpha, beta, pq, rr, r0, tol, rtol, atol;
+  double rz_old;              // (r_{k+1}, z_k) for the flexible variant
+  int iter, done, status, max_it, flexible, use_cond;
+  int guard;                  // WHILE-body executions of this solve (hard stop)
+  unsigned long long cond;    // cudaGraphConditionalHandle of the WHILE node
+  unsigned ticket[4];         // last-block tickets, one per reduction kind
+};
+
+// ---------------------------------------------------------------- vector types
+template <typename T> struct Vec;
+template <> struct Vec<double> { using type = double2; static constexpr int W = 2; };
+template <> struct Vec<float> { using type = float4; static constexpr int W = 4; };
+template <> struct Vec<__nv_bfloat16> { using type = uint4; static constexpr int W = 8; };
+
+template <typename T, int B> struct Pad {
+  static constexpr int VW = Vec<T>::W;
+  static constexpr int KP = ((B * B + VW - 1) / VW) * VW;
+  static constexpr int NCH = KP / VW;
+};
+
+template <typename T> __device__ __forceinline__ void unpack(const typename Vec<T>::type& v, float* out);
+template <> __device__ __forceinline__ void unpack<float>(const float4& v, float* o) {
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+template <> __device__ __forceinline__ void unpack<__nv_bfloat16>(const uint4& v, float* o) {
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    float2 f = __bfloat1622float2(h[t]);
+    o[2 * t] = f.x;
+    o[2 * t + 1] = f.y;
+  }
+}
+
+// Loads chunk `ch` of a sliced block into vals[0..VW) as the accumulation type A.
+template <typename TS, typename A> struct ChunkLoad;
+template <> struct ChunkLoad<double, double> {
+  static constexpr int VW = 2;
+  __device__ __forceinline__ static void load(const double* base, int ch, int lane, double* v) {
+    double2 t = __ldg(reinterpret_cast<const double2*>(base) + (size_t)ch * SL + lane);
+    v[0] = t.x; v[1] = t.y;
+  }
+};
+template <> struct ChunkLoad<float, float> {
+  static constexpr int VW = 4;
+  __device__ __forceinline__ static void load(const float* base, int ch, int lane, float* v) {
+    float4 t = __ldg(reinterpret_cast<const float4*>(base) + (size_t)ch * SL + lane);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+};
+template <> struct ChunkLoad<__nv_bfloat16, float> {
+  static constexpr int VW = 8;
+  __device__ __forceinline__ static void load(const __nv_bfloat16* base, int ch, int lane, float* v) {
+    uint4 t = __ldg(reinterpret_cast<const uint4*>(base) + (size_t)ch * SL + lane);
+    unpack<__nv_bfloat16>(t, v);
+  }
+};
+
+// acc[r] += sum_c M[r][c] x[c] for one sliced block M (storage TS, math A)
+template <typename TS, typename A, int B>
+__device__ __forceinline__ void block_mv(const TS* base, int lane, const A* x, A* acc) {
+  constexpr int VW = ChunkLoad<TS, A>::VW;
+  constexpr int NCH = (B * B + VW - 1) / VW;
+#pragma unroll
+  for (int ch = 0; ch < NCH; ++ch) {
+    A v[VW];
+    ChunkLoad<TS, A>::load(base, ch, lane, v);
+#pragma unroll
+    for (int t = 0; t < VW; ++t) {
+      const int k = ch * VW + t;
+      if (k < B * B) acc[k % B] += v[t] * x[k / B];
+    }
+  }
+}
+// acc[c] += sum_r M[r][c] x[r] (transposed block)
+template <typename TS, typename A, int B>
+__device__ __forceinline__ void block_mtv(const TS* base, int lane, const A* x, A* acc) {
+  constexpr int VW = ChunkLoad<TS, A>::VW;
+  constexpr int NCH = (B * B + VW - 1) / VW;
+#pragma unroll
+  for (int ch = 0; ch < NCH; ++ch) {
+    A v[VW];
+    ChunkLoad<TS, A>::load(base, ch, lane, v);
+#pragma unroll
+    for (int t = 0; t < VW; ++t) {
+      const int k = ch * VW + t;
+      if (k < B * B) acc[k / B] += v[t] * x[k % B];
+    }
+  }
+}
+
+template <typename T>
+struct SellView {
+  const int32_t* slice_ptr;   // [nslices + 1] slot offsets
+  const int32_t* cols;        // [(slot) * 32 + lane]
+  const T* vals;              // [slot][KP * 32]
+  int64_t nslices;
+};
+
+// y_u = sum_slots A_{u,col} x_col for the thread's unit (acc zeroed by caller)
+template <typename T, int B>
+__device__ __forceinline__ void sell_row(const SellView<T>& A, int64_t slice, int lane, const T* __restrict__ x,
+                                         T* acc) {
+  constexpr int KP = Pad<T, B>::KP;
+  const int s0 = A.slice_ptr[slice], s1 = A.slice_ptr[slice + 1];
+  for (int j = s0; j < s1; ++j) {
+    const int col = A.cols[(size_t)j * SL + lane];
+    const T* xb = x + (size_t)col * B;
+    T xv[B];
+#pragma unroll
+    for (int c = 0; c < B; ++c) xv[c] = xb[c];
+    block_mv<T, T, B>(A.vals + (size_t)j * SL * KP, lane, xv, acc);
+  }
+}
+
+// ---------------------------------------------------------------- reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block; result valid in thread 0.
+template <int NTH>
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[NTH / 32];
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (w == 0) {
+    s = (l < NTH / 32) ? sh[l] : 0.0;
+    s = warp_sum(s);
+  }
+  return s;
+}
+
+// Writes this block's partial; returns true in every thread of the last block
+// to finish, which then owns the partials of all blocks (fixed order).
+template <int NTH>
+__device__ __forceinline__ bool partial_and_last(double v, double* partials, unsigned* ticket) {
+  __shared__ bool last;
+  double s = block_sum<NTH>(v);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = s;
+    __threadfence();
+    unsigned t = atomicAdd(ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+template <int NTH>
+__device__ __forceinline__ double sum_partials(const double* partials, int n) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += NTH) s += ((volatile const double*)partials)[i];
+  return block_sum<NTH>(s);
+}
+
+// ---------------------------------------------------------------- SpMV
+// MODE 0: y = A x;  MODE 1: y = rhs - A x;  MODE 2: y = A x and (x, y) -> alpha
+__device__ __forceinline__ void stop_loop(CGState* st) {
+  if (st->use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)st->cond, 0u);
+}
+
+template <typename T, int B, int MODE>
+static __global__ void __launch_bounds__(NT) k_spmv(SellView<T> A, const T* __restrict__ x, const T* __restrict__ rhs,
+                                             T* __restrict__ y, double* partials, CGState* st) {
+  if (MODE == 2) {
+    // head of a PCG iteration: re-assert the loop exit once the solve is done,
+    // and stop unconditionally after max_it + 2 iterations of this loop
+    if (st->done || st->guard > st->max_it + 2) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->done = 1;
+        stop_loop(st);
+      }
+      return;
+    }
+  } else if (st && st->done) {
+    return;
+  }
+  const int64_t unit = (int64_t)blockIdx.x * NT + threadIdx.x;
+  const int64_t slice = unit / SL;
+  const int lane = threadIdx.x & 31;
+  double part = 0.0;
+  if (slice < A.nslices) {
+    T acc[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) acc[r] = T(0);
+    sell_row<T, B>(A, slice, lane, x, acc);
+    T* yb = y + (size_t)unit * B;
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+      if (MODE == 1) {
+        yb[r] = rhs[(size_t)unit * B + r] - acc[r];
+      } else {
+        yb[r] = acc[r];
+        if (MODE == 2) part += (double)x[(size_t)unit * B + r] * (double)acc[r];
+      }
+    }
+  }
+  if (MODE == 2) {
+    if (partial_and_last<NT>(part, partials, &st->ticket[0])) {
+      double pq = sum_partials<NT>(partials, gridDim.x);
+      if (threadIdx.x == 0) {
+        st->pq = pq;
+        st->alpha = st->rho / pq;
+        st->ticket[0] = 0;
+        st->guard += 1;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- Chebyshev step
+// KIND 0: d = c2 Dinv rhs, x_new = d                          (start from x = 0)
+// KIND 1: d = c2 Dinv (rhs - A x_old), x_new = x_old + d      (first step, x given)
+// KIND 2: d = c1 d + c2 Dinv (rhs - A x_old), x_new = x_old + d
+template <typename T, typename TD, int B, int KIND>
+static __global__ void __launch_bounds__(NT) k_cheb(SellView<T> A, const TD* __restrict__ Dinv, const T* __restrict__ rhs,
+                                             const T* __restrict__ x_old, T* __restrict__ x_new, T* __restrict__ d,
+                                             T c1, T c2, int64_t nslices, const CGState* st) {
+  if (st && st->done) return;
+  constexpr int KPD = Pad<TD, B>::KP;
+  const int64_t unit = (int64_t)blockIdx.x * NT + threadIdx.x;
+  const int64_t slice = unit / SL;
+  const int lane = threadIdx.x & 31;
+  if (slice >= nslices) return;
+  const size_t o = (size_t)unit * B;
+  T t[B];
+  if (KIND == 0) {
+#pragma unroll
+    for (int r = 0; r < B; ++r) t[r] = rhs[o + r];
+  } else {
+    T acc[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) acc[r] = T(0);
+    sell_row<T, B>(A, slice, lane, x_old, acc);
+#pragma unroll
+    for (int r = 0; r < B; ++r) t[r] = rhs[o + r] - acc[r];
+  }
+  T s[B];
+#pragma unroll
+  for (int r = 0; r < B; ++r) s[r] = T(0);
+  block_mv<TD, T, B>(Dinv + (size_t)slice * SL * KPD, lane, t, s);
+#pragma unroll
+  for (int r = 0; r < B; ++r) {
+    T dn = (KIND == 2) ? c1 * d[o + r] + c2 * s[r] : c2 * s[r];
+    d[o + r] = dn;
+    x_new[o + r] = (KIND == 0) ? dn : x_old[o + r] + dn;
+  }
+}
+
+// ---------------------------------------------------------------- transfers
+// S_u = P_u^T (rhs_u - (A x)_u): residual of the pre-smoothed iterate, restricted
+template <typename T, int B>
+static __global__ void __launch_bounds__(NT) k_resid_restrict(SellView<T> A, const T* __restrict__ P, const T* __restrict__ rhs,
+                                                       const T* __restrict__ x, T* __restrict__ S, const CGState* st) {
+  if (st && st->done) return;
+  constexpr int KP = Pad<T, B>::KP;
+  const int64_t unit = (int64_t)blockIdx.x * NT + threadIdx.x;
+  const int64_t slice = unit / SL;
+  const int lane = threadIdx.x & 31;
+  if (slice >= A.nslices) return;
+  const size_t o = (size_t)unit * B;
+  T acc[B];
+#pragma unroll
+  for (int r = 0; r < B; ++r) acc[r] = T(0);
+  sell_row<T, B>(A, slice, lane, x, acc);
+  T t[B], s[B];
+#pragma unroll
+  for (int r = 0; r < B; ++r) { t[r] = rhs[o + r] - acc[r]; s[r] = T(0); }
+  block_mtv<T, T, B>(P + (size_t)slice * SL * KP, lane, t, s);
+#pragma unroll
+  for (int j = 0; j < B; ++j) S[o + j] = s[j];
+}
+
+// rc[K*B + j] = sum over the children u of K of S[u*B + j] (children contiguous)
+template <typename T, int B>
+static __global__ void k_segsum(const int64_t* __restrict__ child_ptr, const T* __restrict__ S, T* __restrict__ rc,
+                         int64_t nK, const CGState* st) {
+  if (st && st->done) return;
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= nK * B) return;
+  const int64_t K = id / B;
+  const int j = (int)(id % B);
+  T s = T(0);
+  for (int64_t u = child_ptr[K]; u < child_ptr[K + 1]; ++u) s += S[(size_t)u * B + j];
+  rc[id] = s;
+}
+
+// x_u += P_u e_{parent(u)}
+template <typename T, int B>
+static __global__ void __launch_bounds__(NT) k_prolong(const T* __restrict__ P, const int32_t* __restrict__ parent,
+                                                const T* __restrict__ ec, T* __restrict__ x, int64_t nslices,
+                                                const CGState* st) {
+  if (st && st->done) return;
+  constexpr int KP = Pad<T, B>::KP;
+  const int64_t unit = (int64_t)blockIdx.x * NT + threadIdx.x;
+  const int64_t slice = unit / SL;
+  const int lane = threadIdx.x & 31;
+  if (slice >= nslices) return;
+  const size_t o = (size_t)unit * B;
+  const T* eb = ec + (size_t)parent[unit] * B;
+  T ev[B], acc[B];
+#pragma unroll
+  for (int j = 0; j < B; ++j) { ev[j] = eb[j]; acc[j] = T(0); }
+  block_mv<T, T, B>(P + (size_t)slice * SL * KP, lane, ev, acc);
+#pragma unroll
+  for (int r = 0; r < B; ++r) x[o + r] += acc[r];
+}
+
+// ---------------------------------------------------------------- coarsest solve
+// y = Linv r (lower triangular, row-major), one warp per row
+template <typename T>
+static __global__ void k_coarse_lower(const double* __restrict__ Linv, const T* __restrict__ r, double* __restrict__ y,
+                               int64_t n, const CGState* st) {
+  if (st && st->done) return;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const double* Lr = Linv + (size_t)row * n;
+  double s = 0.0;
+  for (int64_t k = lane; k <= row; k += 32) s += Lr[k] * (double)r[k];
+  s = warp_sum(s);
+  if (lane == 0) y[row] = s;
+}
+// z = Linv^T y using U = Linv^T stored row-major (upper triangular)
+template <typename T>
+static __global__ void k_coarse_upper(const double* __restrict__ U, const double* __restrict__ y, T* __restrict__ z,
+                               int64_t n, const CGState* st) {
+  if (st && st->done) return;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const double* Ur = U + (size_t)row * n;
+  double s = 0.0;
+  for (int64_t k = row + lane; k < n; k += 32) s += Ur[k] * y[k];
+  s = warp_sum(s);
+  if (lane == 0) z[row] = (T)s;
+}
+
+}  // namespace aggmg

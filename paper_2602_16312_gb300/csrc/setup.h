@@ -1,0 +1,89 @@
+// Host-side float64 set-up of the SIPG discretisation and of the
+// agglomerated multigrid hierarchy (run once, before time stepping).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace aggmg {
+
+// Block compressed rows: block row r owns blocks rowptr[r] .. rowptr[r+1]-1,
+// block k sits in column col[k], values val[k*B*B + i*B + j] (row-major).
+struct BlockCSR {
+  int64_t nrows = 0;
+  int B = 0;
+  std::vector<int64_t> rowptr;
+  std::vector<int32_t> col;
+  std::vector<double> val;
+  int64_t nnzb() const { return (int64_t)col.size(); }
+};
+
+// 1D tables of the reference element: GLL nodes of degree p and a q-point
+// Gauss-Legendre rule, both on [0, 1].
+struct Tables1D {
+  int p = 0, q = 0;
+  std::vector<double> gll, gx, gw;
+};
+Tables1D make_tables(int p, int q);
+// values v[i] = l_i(x) and derivatives d[i] = l_i'(x) of the Lagrange
+// polynomials through `nodes` (n entries).
+void lagrange_eval(const double* nodes, int n, double x, double* v, double* d);
+
+struct Mesh {
+  int dim = 0, p = 0, B = 0;
+  int64_t nv = 0, ne = 0;
+  std::vector<double> X;         // [nv][dim]
+  std::vector<int64_t> cells;    // [ne][2^dim]
+  std::vector<double> D;         // [ne][dim][dim]
+  int penalty_mode = 1;
+  double penalty_coeff = 10.0;
+  int quad_extra = 1;
+  BlockCSR A;                    // SIPG stiffness in element order, columns sorted
+  std::vector<double> Me;        // [ne][B][B] element mass blocks
+  std::vector<double> vol;       // [ne]
+  int64_t n_faces = 0;           // interior faces
+};
+
+// Returns 0 or an agg_status; err gets a message.
+int mesh_build(Mesh& m, std::string& err);
+
+struct HostLevel {
+  int64_t n = 0;                       // units on this level
+  std::vector<int64_t> perm;           // internal index -> caller's id
+  std::vector<int64_t> inv;            // caller's id -> internal index
+  BlockCSR A;                          // level operator, internal order
+  std::vector<double> Dinv;            // [n][B][B] smoother block inverses
+  double lam_hat = 0, lam_max = 0, lam_min = 0;
+  // transfer to the next coarser level (absent on the coarsest)
+  std::vector<double> P;               // [n][B][B]: P[u][i][j] = phi_j^{parent}(y_{u,i})
+  std::vector<int32_t> parent;         // internal index on level l+1
+  // children of this level's units on the finer level (absent on level 0)
+  std::vector<int64_t> child_ptr;      // [n+1], children are contiguous
+  std::vector<double> lo, hi;          // bounding boxes (levels >= 1)
+  std::vector<double> nodes;           // [n][B][dim] nodal points y_{u,i}
+};
+
+struct HostHierarchy {
+  int L = 0, B = 0, dim = 0, p = 0;
+  double mass_coeff = 0;
+  std::vector<HostLevel> lev;
+  int64_t nc = 0;                      // coarsest DoFs
+  std::vector<double> Linv;            // [nc][nc] inverse Cholesky factor, row-major
+};
+
+struct HierOptions {
+  int L = 1;
+  const int32_t* const* maps = nullptr;
+  int degree = 3;
+  bool block_jacobi = true;
+  int lanczos_steps = 12;
+  double safety = 1.2, range = 20.0;
+};
+
+int hierarchy_build(const Mesh& m, double mass_coeff, const HierOptions& o, HostHierarchy& h,
+                    std::string& err);
+
+// y = A x on the host (block CSR, float64)
+void bsr_apply(const BlockCSR& A, const double* x, double* y);
+
+}  // namespace aggmg

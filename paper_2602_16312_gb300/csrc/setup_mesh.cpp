@@ -1,0 +1,508 @@
+// Host float64 assembly of the SIPG-DG operator (Section 3 of arXiv 2602.16312):
+// reference element tables, element mass/stiffness blocks, face matching and
+// the interior-face terms of a_h, assembled as a block-CSR matrix in element
+// order. Parallel over elements with OpenMP; every block row is written by
+// the thread that owns the element, so the result does not depend on the
+// thread count.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+
+#include "setup.h"
+#include "../../include/aggmg.h"
+
+namespace aggmg {
+
+// ---------------------------------------------------------------- 1D tables
+// Legendre P_n(x) and P_n'(x) on [-1, 1] by the three-term recurrence.
+static void legendre(int n, double x, double& P, double& dP) {
+  double p0 = 1.0, p1 = x;
+  if (n == 0) { P = 1.0; dP = 0.0; return; }
+  for (int k = 2; k <= n; ++k) {
+    double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+    p0 = p1;
+    p1 = p2;
+  }
+  P = p1;
+  dP = n * (x * p1 - p0) / (x * x - 1.0);
+}
+
+Tables1D make_tables(int p, int q) {
+  Tables1D t;
+  t.p = p;
+  t.q = q;
+  // Gauss-Legendre: Newton on P_q from the standard asymptotic starting values
+  std::vector<double> x(q), w(q);
+  for (int i = 0; i < q; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (q + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre(q, z, P, dP);
+      double dz = P / dP;
+      z -= dz;
+      if (std::fabs(dz) < 1e-17) break;
+    }
+    double P, dP;
+    legendre(q, z, P, dP);
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dP * dP);
+  }
+  std::vector<int> ord(q);
+  for (int i = 0; i < q; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](int a, int b) { return x[a] < x[b]; });
+  for (int i = 0; i < q; ++i) {
+    t.gx.push_back(0.5 * (x[ord[i]] + 1.0));
+    t.gw.push_back(0.5 * w[ord[i]]);
+  }
+  // Gauss-Lobatto: end points and the roots of P_p', Newton with
+  // P_p'' = (2 x P_p' - p(p+1) P_p) / (1 - x^2) (Legendre's equation)
+  std::vector<double> g;
+  g.push_back(-1.0);
+  for (int i = p - 1; i >= 1; --i) {
+    double z = std::cos(M_PI * i / p);
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre(p, z, P, dP);
+      double d2P = (2.0 * z * dP - p * (p + 1.0) * P) / (1.0 - z * z);
+      double dz = dP / d2P;
+      z -= dz;
+      if (std::fabs(dz) < 1e-17) break;
+    }
+    g.push_back(z);
+  }
+  g.push_back(1.0);
+  std::sort(g.begin(), g.end());
+  for (double z : g) t.gll.push_back(0.5 * (z + 1.0));
+  return t;
+}
+
+void lagrange_eval(const double* nodes, int n, double x, double* v, double* d) {
+  for (int i = 0; i < n; ++i) {
+    double prod = 1.0;
+    for (int m = 0; m < n; ++m)
+      if (m != i) prod *= (x - nodes[m]) / (nodes[i] - nodes[m]);
+    v[i] = prod;
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) {
+      if (k == i) continue;
+      double term = 1.0 / (nodes[i] - nodes[k]);
+      for (int m = 0; m < n; ++m)
+        if (m != i && m != k) term *= (x - nodes[m]) / (nodes[i] - nodes[m]);
+      s += term;
+    }
+    d[i] = s;
+  }
+}
+
+// ---------------------------------------------------------------- element geometry
+namespace {
+
+constexpr int MAXD = 3;
+constexpr int MAXB = 125;   // (4+1)^3
+
+struct Basis {               // tensor basis values and reference gradients at one point
+  double phi[MAXB];
+  double g[MAXB][MAXD];
+};
+
+void tensor_basis(const Tables1D& t, int dim, const double* xi, Basis& out) {
+  int n1 = t.p + 1;
+  double v[MAXD][8], d[MAXD][8];
+  for (int k = 0; k < dim; ++k) lagrange_eval(t.gll.data(), n1, xi[k], v[k], d[k]);
+  int B = 1;
+  for (int k = 0; k < dim; ++k) B *= n1;
+  for (int i = 0; i < B; ++i) {
+    int idx[MAXD];
+    int r = i;
+    for (int k = 0; k < dim; ++k) { idx[k] = r % n1; r /= n1; }
+    double ph = 1.0;
+    for (int k = 0; k < dim; ++k) ph *= v[k][idx[k]];
+    out.phi[i] = ph;
+    for (int l = 0; l < dim; ++l) {
+      double gl = 1.0;
+      for (int k = 0; k < dim; ++k) gl *= (k == l) ? d[k][idx[k]] : v[k][idx[k]];
+      out.g[i][l] = gl;
+    }
+  }
+}
+
+// multilinear map: x(xi) and J[k][l] = dx_k/dxi_l from the 2^dim corners
+void map_point(int dim, const double* Xc, const double* xi, double* x, double J[MAXD][MAXD]) {
+  int V = 1 << dim;
+  for (int k = 0; k < dim; ++k) {
+    x[k] = 0.0;
+    for (int l = 0; l < dim; ++l) J[k][l] = 0.0;
+  }
+  for (int c = 0; c < V; ++c) {
+    double N = 1.0;
+    double dN[MAXD];
+    for (int l = 0; l < dim; ++l) dN[l] = 1.0;
+    for (int k = 0; k < dim; ++k) {
+      int bit = (c >> k) & 1;
+      double f = bit ? xi[k] : 1.0 - xi[k];
+      double df = bit ? 1.0 : -1.0;
+      N *= f;
+      for (int l = 0; l < dim; ++l) dN[l] *= (l == k) ? df : f;
+    }
+    for (int k = 0; k < dim; ++k) {
+      x[k] += N * Xc[c * dim + k];
+      for (int l = 0; l < dim; ++l) J[k][l] += dN[l] * Xc[c * dim + k];
+    }
+  }
+}
+
+double det_inv(int dim, double J[MAXD][MAXD], double Ji[MAXD][MAXD]) {
+  if (dim == 2) {
+    double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    Ji[0][0] = J[1][1] / det;
+    Ji[0][1] = -J[0][1] / det;
+    Ji[1][0] = -J[1][0] / det;
+    Ji[1][1] = J[0][0] / det;
+    return det;
+  }
+  double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+  Ji[0][0] = c00 / det;
+  Ji[1][0] = c01 / det;
+  Ji[2][0] = c02 / det;
+  Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+  Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+  Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+  Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+  Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+  Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+  return det;
+}
+
+// physical gradient: component k = sum_l Jinv[l][k] * ghat_l
+inline void phys_grad(int dim, const double Ji[MAXD][MAXD], const double* gh, double* g) {
+  for (int k = 0; k < dim; ++k) {
+    double s = 0.0;
+    for (int l = 0; l < dim; ++l) s += Ji[l][k] * gh[l];
+    g[k] = s;
+  }
+}
+
+// corners of local face f = 2k + s, in face-corner order (lowest remaining axis fastest)
+int face_corners(int dim, int f, int* out) {
+  int k = f / 2, s = f % 2;
+  int others[MAXD], no = 0;
+  for (int a = 0; a < dim; ++a)
+    if (a != k) others[no++] = a;
+  int nvf = 1 << (dim - 1);
+  for (int m = 0; m < nvf; ++m) {
+    int c = s << k;
+    for (int j = 0; j < no; ++j) c |= ((m >> j) & 1) << others[j];
+    out[m] = c;
+  }
+  return nvf;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- assembly
+int mesh_build(Mesh& m, std::string& err) {
+  const int dim = m.dim, p = m.p;
+  if (dim != 2 && dim != 3) { err = "dim must be 2 or 3"; return AGG_EINVAL; }
+  if (p < 1 || p > 4) { err = "degree must be in 1..4"; return AGG_EINVAL; }
+  if (m.quad_extra < 0 || m.quad_extra > 4) { err = "quad_extra must be in 0..4"; return AGG_EINVAL; }
+  const int n1 = p + 1;
+  int B = 1;
+  for (int k = 0; k < dim; ++k) B *= n1;
+  m.B = B;
+  const int V = 1 << dim;
+  const int64_t ne = m.ne;
+  for (int64_t i = 0; i < ne * V; ++i)
+    if (m.cells[i] < 0 || m.cells[i] >= m.nv) { err = "vertex id out of range"; return AGG_EINVAL; }
+  const double c_pen = (m.penalty_mode == 0) ? double(p * (p + 1)) : m.penalty_coeff * p * p;
+
+  const int q = p + 1 + m.quad_extra;
+  Tables1D t = make_tables(p, q);
+  // volume quadrature: tensor Gauss points, x fastest
+  int Q = 1;
+  for (int k = 0; k < dim; ++k) Q *= q;
+  std::vector<double> qx(Q * dim), qw(Q);
+  for (int iq = 0; iq < Q; ++iq) {
+    int r = iq;
+    double w = 1.0;
+    for (int k = 0; k < dim; ++k) {
+      int a = r % q;
+      r /= q;
+      qx[iq * dim + k] = t.gx[a];
+      w *= t.gw[a];
+    }
+    qw[iq] = w;
+  }
+  std::vector<Basis> qb(Q);
+  for (int iq = 0; iq < Q; ++iq) tensor_basis(t, dim, &qx[iq * dim], qb[iq]);
+  // face quadrature: tensor Gauss in dim-1 coordinates
+  int Qf = 1;
+  for (int k = 0; k < dim - 1; ++k) Qf *= q;
+  std::vector<double> ft(Qf * MAXD), fw(Qf);
+  for (int iq = 0; iq < Qf; ++iq) {
+    int r = iq;
+    double w = 1.0;
+    for (int k = 0; k < dim - 1; ++k) {
+      int a = r % q;
+      r /= q;
+      ft[iq * MAXD + k] = t.gx[a];
+      w *= t.gw[a];
+    }
+    fw[iq] = w;
+  }
+
+  m.Me.assign((size_t)ne * B * B, 0.0);
+  std::vector<double> Ke((size_t)ne * B * B, 0.0);
+  m.vol.assign(ne, 0.0);
+  int bad_jac = 0;
+
+#pragma omp parallel for schedule(static) reduction(+ : bad_jac)
+  for (int64_t e = 0; e < ne; ++e) {
+    double Xc[8 * MAXD];
+    for (int c = 0; c < V; ++c)
+      for (int k = 0; k < dim; ++k) Xc[c * dim + k] = m.X[m.cells[e * V + c] * dim + k];
+    const double* De = &m.D[e * dim * dim];
+    double* Mb = &m.Me[(size_t)e * B * B];
+    double* Kb = &Ke[(size_t)e * B * B];
+    double vol = 0.0;
+    std::vector<double> G((size_t)B * MAXD), DG((size_t)B * MAXD);
+    for (int iq = 0; iq < Q; ++iq) {
+      double x[MAXD], J[MAXD][MAXD], Ji[MAXD][MAXD];
+      map_point(dim, Xc, &qx[iq * dim], x, J);
+      double det = det_inv(dim, J, Ji);
+      if (!(det > 0.0)) { bad_jac += 1; continue; }
+      double wJ = qw[iq] * det;
+      vol += wJ;
+      const Basis& b = qb[iq];
+      for (int i = 0; i < B; ++i) {
+        phys_grad(dim, Ji, b.g[i], &G[i * MAXD]);
+        for (int k = 0; k < dim; ++k) {
+          double s = 0.0;
+          for (int l = 0; l < dim; ++l) s += De[k * dim + l] * G[i * MAXD + l];
+          DG[i * MAXD + k] = s;
+        }
+      }
+      for (int i = 0; i < B; ++i)
+        for (int j = 0; j < B; ++j) {
+          Mb[i * B + j] += wJ * b.phi[i] * b.phi[j];
+          double s = 0.0;
+          for (int k = 0; k < dim; ++k) s += G[i * MAXD + k] * DG[j * MAXD + k];
+          Kb[i * B + j] += wJ * s;
+        }
+    }
+    m.vol[e] = vol;
+  }
+  if (bad_jac) { err = "element with non-positive Jacobian"; return AGG_EINVAL; }
+
+  // ---------------- face matching by sorted vertex ids
+  const int nf = 2 * dim;
+  const int nvf = 1 << (dim - 1);
+  int fcorn[6][4];
+  for (int f = 0; f < nf; ++f) face_corners(dim, f, fcorn[f]);
+  struct Key {
+    std::array<int64_t, 4> v;
+    int64_t rec;
+  };
+  std::vector<Key> keys((size_t)ne * nf);
+#pragma omp parallel for schedule(static)
+  for (int64_t e = 0; e < ne; ++e)
+    for (int f = 0; f < nf; ++f) {
+      Key& k = keys[e * nf + f];
+      k.v = {-1, -1, -1, -1};
+      for (int mm = 0; mm < nvf; ++mm) k.v[mm] = m.cells[e * V + fcorn[f][mm]];
+      std::sort(k.v.begin(), k.v.begin() + nvf);
+      k.rec = e * nf + f;
+    }
+  std::sort(keys.begin(), keys.end(), [](const Key& a, const Key& b) {
+    if (a.v != b.v) return a.v < b.v;
+    return a.rec < b.rec;
+  });
+  std::vector<int64_t> nbr((size_t)ne * nf, -1);   // neighbour record e'*nf + f'
+  int64_t nint = 0;
+  for (size_t i = 0; i < keys.size();) {
+    size_t j = i + 1;
+    while (j < keys.size() && keys[j].v == keys[i].v) ++j;
+    if (j - i == 2) {
+      nbr[keys[i].rec] = keys[i + 1].rec;
+      nbr[keys[i + 1].rec] = keys[i].rec;
+      ++nint;
+    } else if (j - i > 2) {
+      err = "a face is shared by more than two elements";
+      return AGG_EINVAL;
+    }
+    i = j;
+  }
+  m.n_faces = nint;
+
+  // ---------------- block rows: diagonal + one block per interior face
+  m.A.nrows = ne;
+  m.A.B = B;
+  m.A.rowptr.assign(ne + 1, 0);
+  for (int64_t e = 0; e < ne; ++e) {
+    int cnt = 1;
+    for (int f = 0; f < nf; ++f) cnt += nbr[e * nf + f] >= 0;
+    m.A.rowptr[e + 1] = m.A.rowptr[e] + cnt;
+  }
+  const int64_t nnzb = m.A.rowptr[ne];
+  m.A.col.assign(nnzb, 0);
+  m.A.val.assign((size_t)nnzb * B * B, 0.0);
+  int bad_face = 0;
+
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : bad_face)
+  for (int64_t e = 0; e < ne; ++e) {
+    // column order: sorted neighbour ids (diagonal included)
+    int64_t cols[7];
+    int fof[7];
+    int nc = 0;
+    cols[nc] = e;
+    fof[nc++] = -1;
+    for (int f = 0; f < nf; ++f)
+      if (nbr[e * nf + f] >= 0) {
+        cols[nc] = nbr[e * nf + f] / nf;
+        fof[nc++] = f;
+      }
+    int ord[7];
+    for (int i = 0; i < nc; ++i) ord[i] = i;
+    std::sort(ord, ord + nc, [&](int a, int b) { return cols[a] < cols[b]; });
+    const int64_t base = m.A.rowptr[e];
+    int diag_slot = -1;
+    int slot_of[7];
+    for (int s = 0; s < nc; ++s) {
+      m.A.col[base + s] = (int32_t)cols[ord[s]];
+      slot_of[ord[s]] = s;
+      if (ord[s] == 0) diag_slot = s;
+    }
+    double* Adiag = &m.A.val[(size_t)(base + diag_slot) * B * B];
+    std::memcpy(Adiag, &Ke[(size_t)e * B * B], sizeof(double) * B * B);
+
+    double Xp[8 * MAXD], Xm[8 * MAXD];
+    for (int c = 0; c < V; ++c)
+      for (int k = 0; k < dim; ++k) Xp[c * dim + k] = m.X[m.cells[e * V + c] * dim + k];
+    const double* Dp = &m.D[e * dim * dim];
+    std::vector<double> php(B), phm(B), flp(B), flm(B), sig(Qf), wdS(Qf);
+    std::vector<double> PHP((size_t)Qf * B), PHM((size_t)Qf * B), FLP((size_t)Qf * B),
+        FLM((size_t)Qf * B);
+    for (int i = 1; i < nc; ++i) {
+      const int f = fof[i];
+      const int64_t rec = nbr[e * nf + f];
+      const int64_t n = rec / nf;
+      const int fn = (int)(rec % nf);
+      for (int c = 0; c < V; ++c)
+        for (int k = 0; k < dim; ++k) Xm[c * dim + k] = m.X[m.cells[n * V + c] * dim + k];
+      const double* Dm = &m.D[n * dim * dim];
+      // reference coordinates on the neighbour of each face corner of e
+      double cxi[4][MAXD];
+      for (int mm = 0; mm < nvf; ++mm) {
+        int64_t gid = m.cells[e * V + fcorn[f][mm]];
+        int found = -1;
+        for (int mk = 0; mk < nvf; ++mk)
+          if (m.cells[n * V + fcorn[fn][mk]] == gid) found = fcorn[fn][mk];
+        if (found < 0) { bad_face += 1; found = 0; }
+        for (int k = 0; k < dim; ++k) cxi[mm][k] = (found >> k) & 1;
+      }
+      const int kf = f / 2, sf = f % 2;
+      int others[MAXD], no = 0;
+      for (int a = 0; a < dim; ++a)
+        if (a != kf) others[no++] = a;
+      double area = 0.0;
+      std::vector<std::array<double, MAXD>> nrm(Qf);
+      for (int iq = 0; iq < Qf; ++iq) {
+        const double* tq = &ft[iq * MAXD];
+        double xip[MAXD], xim[MAXD];
+        xip[kf] = sf;
+        for (int j = 0; j < no; ++j) xip[others[j]] = tq[j];
+        for (int k = 0; k < dim; ++k) xim[k] = 0.0;
+        for (int mm = 0; mm < nvf; ++mm) {
+          double Nf = 1.0;
+          for (int j = 0; j < dim - 1; ++j) Nf *= ((mm >> j) & 1) ? tq[j] : 1.0 - tq[j];
+          for (int k = 0; k < dim; ++k) xim[k] += Nf * cxi[mm][k];
+        }
+        double xp[MAXD], xm[MAXD], Jp[MAXD][MAXD], Jm[MAXD][MAXD], Jip[MAXD][MAXD], Jim[MAXD][MAXD];
+        map_point(dim, Xp, xip, xp, Jp);
+        map_point(dim, Xm, xim, xm, Jm);
+        double detp = det_inv(dim, Jp, Jip);
+        det_inv(dim, Jm, Jim);
+        double dist = 0.0, scale = 1.0;
+        for (int k = 0; k < dim; ++k) {
+          dist = std::max(dist, std::fabs(xp[k] - xm[k]));
+          scale = std::max(scale, std::fabs(xp[k]));
+        }
+        if (dist > 1e-10 * scale) bad_face += 1;
+        double nv[MAXD], len = 0.0;
+        for (int k = 0; k < dim; ++k) {
+          nv[k] = Jip[kf][k] * (2.0 * sf - 1.0);      // J^{-T} nhat
+          len += nv[k] * nv[k];
+        }
+        len = std::sqrt(len);
+        for (int k = 0; k < dim; ++k) nrm[iq][k] = nv[k] / len;
+        wdS[iq] = fw[iq] * detp * len;
+        area += wdS[iq];
+        Basis bp, bm;
+        tensor_basis(t, dim, xip, bp);
+        tensor_basis(t, dim, xim, bm);
+        for (int j = 0; j < B; ++j) {
+          double gp[MAXD], gm[MAXD];
+          phys_grad(dim, Jip, bp.g[j], gp);
+          phys_grad(dim, Jim, bm.g[j], gm);
+          double fp = 0.0, fm = 0.0;
+          for (int k = 0; k < dim; ++k)
+            for (int l = 0; l < dim; ++l) {
+              fp += nrm[iq][k] * Dp[k * dim + l] * gp[l];
+              fm += nrm[iq][k] * Dm[k * dim + l] * gm[l];
+            }
+          PHP[iq * B + j] = bp.phi[j];
+          PHM[iq * B + j] = bm.phi[j];
+          FLP[iq * B + j] = fp;
+          FLM[iq * B + j] = fm;
+        }
+      }
+      const double alpha = c_pen * std::max(area / m.vol[e], area / m.vol[n]);
+      for (int iq = 0; iq < Qf; ++iq) {
+        double s = 0.0;
+        for (int k = 0; k < dim; ++k)
+          for (int l = 0; l < dim; ++l) s += nrm[iq][k] * 0.5 * (Dp[k * dim + l] + Dm[k * dim + l]) * nrm[iq][l];
+        sig[iq] = alpha * s;
+      }
+      double* Aoff = &m.A.val[(size_t)(base + slot_of[i]) * B * B];
+      for (int a = 0; a < B; ++a)
+        for (int b = 0; b < B; ++b) {
+          double spp = 0.0, spm = 0.0;
+          for (int iq = 0; iq < Qf; ++iq) {
+            const double ia = PHP[iq * B + a], fa = FLP[iq * B + a];
+            spp += wdS[iq] * (-0.5 * ia * FLP[iq * B + b] - 0.5 * PHP[iq * B + b] * fa +
+                              sig[iq] * ia * PHP[iq * B + b]);
+            spm += wdS[iq] * (-0.5 * ia * FLM[iq * B + b] + 0.5 * PHM[iq * B + b] * fa -
+                              sig[iq] * ia * PHM[iq * B + b]);
+          }
+          Adiag[a * B + b] += spp;
+          Aoff[a * B + b] = spm;
+        }
+    }
+  }
+  if (bad_face) { err = "non-conforming face (quadrature points do not coincide)"; return AGG_EINVAL; }
+  return AGG_OK;
+}
+
+void bsr_apply(const BlockCSR& A, const double* x, double* y) {
+  const int B = A.B;
+#pragma omp parallel for schedule(static)
+  for (int64_t r = 0; r < A.nrows; ++r) {
+    double acc[MAXB];
+    for (int i = 0; i < B; ++i) acc[i] = 0.0;
+    for (int64_t k = A.rowptr[r]; k < A.rowptr[r + 1]; ++k) {
+      const double* blk = &A.val[(size_t)k * B * B];
+      const double* xc = x + (int64_t)A.col[k] * B;
+      for (int i = 0; i < B; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < B; ++j) s += blk[i * B + j] * xc[j];
+        acc[i] += s;
+      }
+    }
+    for (int i = 0; i < B; ++i) y[r * B + i] = acc[i];
+  }
+}
+
+}  // namespace aggmg
