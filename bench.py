@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=8)
+    ap.add_argument("--profile-kernel", type=int, default=None,
+                    help="set up, launch kernel id K three times (for ncu) and exit")
     return ap.parse_args()
 
 
@@ -182,6 +184,11 @@ def run_ours(args, rank, world):
     mesh = aggmg.Mesh.from_workload(wl)
     hier = aggmg.Hierarchy(mesh, 1.0 / wl.dt, wl.maps, precision=args.form)
     setup_s = time.time() - t0
+    if args.profile_kernel is not None:
+        hier.profile_kernel(args.profile_kernel, 3)
+        torch.cuda.synchronize()
+        hier.close()
+        return
     mask = torch.tensor(wl.stim_mask_nodal(), dtype=torch.float64, device=dev)
     flexible = args.form != "f64"
     sim = aggmg.Monodomain(hier, wl.dt, wl.ionic, iapp_mask=mask, iapp_value=wl.iapp_value,
@@ -262,8 +269,10 @@ def run_ours(args, rank, world):
     st = hier.stats()
     L = hier.n_levels
     vcyc = (L - 1) * 9 + 2
-    per_iter = 5 + vcyc + (1 if args.form != "f64" else 0)
+    per_iter = 6 + vcyc + (1 if args.form != "f64" else 0)
     n_iter = sum(its)
+    # per step: ionic/RHS, set-up (begin, residual, norm, V-cycle, dot, p, loop control),
+    # one body per iteration (the body that detects convergence included), step end
     launches = args.steps * (1 + per_iter + 1) + n_iter * per_iter + 5
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -276,7 +285,7 @@ def run_ours(args, rank, world):
         "config": {"workload": workload_name(wl), "form": args.form, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (fine float64 matrix 0.85 GB, 129 MB L2)",
                    "levels": st["units"], "op_complexity": st["op_complexity"], "setup_s": setup_s,
-                   "conditional_graph": True, "flexible_cg": flexible},
+                   "conditional_graph": os.environ.get("AGG_NO_COND_GRAPH") is None, "flexible_cg": flexible},
         "iterations": {"mean": float(np.mean(its)), "min": int(min(its)), "max": int(max(its)),
                        "std": float(np.std(its)), "warmup": its_w},
         "e2e": {"value": args.e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * N * 8,
@@ -320,6 +329,8 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank)
         return
+    if args.profile_kernel is not None:
+        args.no_cpu_baseline = True
     if world > 1:
         import torch
         import torch.distributed as dist

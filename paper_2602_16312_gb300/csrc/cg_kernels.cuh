@@ -10,7 +10,17 @@ namespace aggmg {
 
 enum { TK_PQ = 0, TK_R = 1, TK_Z = 2, TK_R0 = 3 };
 
-__device__ __forceinline__ void finish_cond(CGState* st) { stop_loop(st); }
+// Loop control of the WHILE node, launched after the PCG set-up and at the end
+// of every iteration: ends the loop once the solve is done, and after
+// max_it + 2 iterations in any case. It is the only kernel that calls the
+// device-side graph API, so every compute kernel stays visible to profilers.
+static __global__ void k_loop_ctl(CGState* st) {
+  if (st->done || st->guard >= st->max_it + 2) {
+    st->done = 1;
+    if (st->use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)st->cond, 0u);
+  }
+  st->guard += 1;
+}
 
 // Reset of the per-solve fields; the options (rtol, atol, max_it, flexible,
 // cond, use_cond) are written by the host before the launch.
@@ -59,10 +69,8 @@ static __global__ void __launch_bounds__(RED_NT) k_r0(const double* __restrict__
       if (!isfinite(st->r0)) {
         st->status = -6;
         st->done = 1;
-        finish_cond(st);
       } else if (st->r0 <= st->tol || st->r0 == 0.0) {
         st->done = 1;
-        finish_cond(st);
       }
     }
   }
@@ -97,7 +105,6 @@ static __global__ void __launch_bounds__(RED_NT) k_cg_update(double* __restrict_
         st->status = -5;
         st->done = 1;
       }
-      if (st->done) finish_cond(st);
     }
   }
 }

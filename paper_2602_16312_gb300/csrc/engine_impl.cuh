@@ -218,12 +218,14 @@ class Engine : public EngineBase {
     k_spmv<double, B, 1><<<g0(), NT, 0, s>>>(A0_, x_, b_, r_, nullptr, nullptr);
     k_r0<<<RED_BLOCKS, RED_NT, 0, s>>>(r_, N0(), partials_, st_);
     launch_precond(s, true);
+    k_loop_ctl<<<1, 1, 0, s>>>(st_);
   }
 
   void launch_body(cudaStream_t s) {
     k_spmv<double, B, 2><<<g0(), NT, 0, s>>>(A0_, p_, nullptr, q_, partials_, st_);
     k_cg_update<<<RED_BLOCKS, RED_NT, 0, s>>>(x_, r_, p_, q_, N0(), partials_, st_);
     launch_precond(s, false);
+    k_loop_ctl<<<1, 1, 0, s>>>(st_);
   }
 
   void launch_step_prologue(cudaStream_t s) {

@@ -193,26 +193,10 @@ __device__ __forceinline__ double sum_partials(const double* partials, int n) {
 
 // ---------------------------------------------------------------- SpMV
 // MODE 0: y = A x;  MODE 1: y = rhs - A x;  MODE 2: y = A x and (x, y) -> alpha
-__device__ __forceinline__ void stop_loop(CGState* st) {
-  if (st->use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)st->cond, 0u);
-}
-
 template <typename T, int B, int MODE>
 static __global__ void __launch_bounds__(NT) k_spmv(SellView<T> A, const T* __restrict__ x, const T* __restrict__ rhs,
                                              T* __restrict__ y, double* partials, CGState* st) {
-  if (MODE == 2) {
-    // head of a PCG iteration: re-assert the loop exit once the solve is done,
-    // and stop unconditionally after max_it + 2 iterations of this loop
-    if (st->done || st->guard > st->max_it + 2) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) {
-        st->done = 1;
-        stop_loop(st);
-      }
-      return;
-    }
-  } else if (st && st->done) {
-    return;
-  }
+  if (st && st->done) return;
   const int64_t unit = (int64_t)blockIdx.x * NT + threadIdx.x;
   const int64_t slice = unit / SL;
   const int lane = threadIdx.x & 31;
@@ -240,7 +224,6 @@ static __global__ void __launch_bounds__(NT) k_spmv(SellView<T> A, const T* __re
         st->pq = pq;
         st->alpha = st->rho / pq;
         st->ticket[0] = 0;
-        st->guard += 1;
       }
     }
   }
