@@ -153,6 +153,31 @@ agg_status agg_operator_apply(agg_hier_t hier, int level, const double* x_dev, d
 /* z = B r: one V-cycle of the preconditioner (Section 6). */
 agg_status agg_vcycle_apply(agg_hier_t hier, const double* r_dev, double* z_dev, void* stream);
 
+/* ------------------------------------------------------------------ allocation-free product
+ * agg_operator_apply_static: the same product y = A_l x as agg_operator_apply
+ * (same operator, same kernels, same results), for callers that must not
+ * allocate device memory at the time of the call: code running while a CUDA
+ * stream is captured into a graph (allocation is not allowed inside a
+ * capture), or an embedding that fixes its device-memory budget at start-up.
+ * It has no counterpart in the paper: it only changes where the two
+ * temporary, unit-permuted copies of x and y live.
+ *
+ * Scratch: one file-scope device array of 2 x AGG_STATIC_APPLY_MAX_ENTRIES
+ * doubles (16 MiB), which every GPU that loads the library holds until the
+ * process exits. The call calls no cudaMalloc, cudaFree or other allocating
+ * routine. Levels 0 .. n_levels-2 only; a level whose padded vector length
+ * ((units rounded up to 32) * (p+1)^d) exceeds AGG_STATIC_APPLY_MAX_ENTRIES
+ * returns AGG_EINVAL. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, once per device, with that device current);
+ * make that first call before any stream capture. The array is shared by all
+ * calls and keeps the last call's contents; nothing in it has to start at
+ * zero (each call writes every entry it reads). Calls that overlap on the
+ * GPU (two streams, or two threads) race on the array: order them on one
+ * stream. */
+#define AGG_STATIC_APPLY_MAX_ENTRIES (1LL << 20)
+agg_status agg_operator_apply_static(agg_hier_t hier, int level, const double* x_dev, double* y_dev,
+                                     void* stream);
+
 /* ------------------------------------------------------------------ ionic models */
 typedef enum { AGG_FHN = 0, AGG_ALIEV_PANFILOV = 1 } agg_ionic_model;
 

@@ -76,6 +76,7 @@ _SIGS = {
     "agg_pcg_solve": [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(PCGOpts), C.POINTER(PCGResult), C.c_void_p],
     "agg_operator_apply": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p],
     "agg_vcycle_apply": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "agg_operator_apply_static": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p],
     "agg_ionic_update": [C.POINTER(IonicParams), C.c_double, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
     "agg_monodomain_create": [C.c_void_p, C.POINTER(SimOpts), C.POINTER(C.c_void_p)],
     "agg_monodomain_step": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.c_void_p],
@@ -299,6 +300,12 @@ class Hierarchy:
     def operator_apply(self, level, x, y, stream=None):
         _check(lib().agg_operator_apply(self.handle, level, C.c_void_p(_dptr(x)), C.c_void_p(_dptr(y)),
                                         C.c_void_p(_stream(stream))))
+
+    def operator_apply_static(self, level, x, y, stream=None):
+        """agg_operator_apply_static: same product, scratch in the library's
+        static device array (no allocation during the call)."""
+        _check(lib().agg_operator_apply_static(self.handle, level, C.c_void_p(_dptr(x)), C.c_void_p(_dptr(y)),
+                                               C.c_void_p(_stream(stream))))
 
     def vcycle_apply(self, r, z, stream=None):
         _check(lib().agg_vcycle_apply(self.handle, C.c_void_p(_dptr(r)), C.c_void_p(_dptr(z)),

@@ -11,6 +11,7 @@
 #include "../../include/aggmg.h"
 #include "cg_kernels.cuh"
 #include "engine.h"
+#include "handles.h"
 #include "setup.h"
 
 namespace aggmg {
@@ -34,20 +35,7 @@ EngineBase* make_engine(int B, int precision) {
 
 using namespace aggmg;
 
-struct agg_mesh {
-  Mesh m;
-};
 
-struct agg_hier {
-  agg_mesh* mesh = nullptr;
-  int device = 0;
-  int L = 0, B = 0, precision = 0;
-  double mass_coeff = 0;
-  std::vector<int64_t> units, nnzb, perm0;
-  std::vector<double> lam_max;
-  EngineBase* eng = nullptr;
-  bool sim_active = false;
-};
 
 struct agg_sim {
   agg_hier* h = nullptr;
@@ -62,6 +50,13 @@ agg_status fail(agg_status s, const std::string& msg) {
   return s;
 }
 
+}  // namespace
+
+namespace aggmg {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace aggmg
+
+namespace {
 agg_status check_device(const agg_hier* h) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);

@@ -48,8 +48,15 @@ class EngineBase {
   // buffers, and its algorithmic bytes / flops per launch
   virtual int kernel_loop(int id, int reps, cudaStream_t s, std::string& err) = 0;
   virtual int kernel_cost(int id, double& bytes, double& flops) const = 0;
+  // y = A_l x with the permuted copies of x and y in caller-provided device
+  // scratch (s_in, s_out: at least level_scratch_entries(l) doubles each)
+  virtual int64_t level_scratch_entries(int level) const = 0;
+  virtual int apply_level_scratch(int level, const double* x_user, double* y_user, void* s_in, void* s_out,
+                                  cudaStream_t s, std::string& err) = 0;
 };
 
 EngineBase* make_engine(int B, int precision);
+// records the calling thread's last error message (read by agg_last_error)
+void set_last_error(const std::string& msg);
 
 }  // namespace aggmg

@@ -476,6 +476,33 @@ class Engine : public EngineBase {
     return AGG_OK;
   }
 
+  int64_t level_scratch_entries(int l) const override {
+    if (l < 0 || l >= nlev_) return -1;
+    return lev_[l].nvec;
+  }
+
+  int apply_level_scratch(int l, const double* x_user, double* y_user, void* s_in, void* s_out, cudaStream_t s,
+                          std::string& err) override {
+    if (l < 0 || l >= nlev_ - 1) { err = "level out of range (the coarsest level has no stored operator)"; return AGG_EINVAL; }
+    Lev& v = lev_[l];
+    const int64_t g = cdiv(v.n * B, 256);
+    if (l == 0) {
+      double* xi = static_cast<double*>(s_in);
+      double* yi = static_cast<double*>(s_out);
+      k_gather_units<double, double><<<g, 256, 0, s>>>(x_user, xi, v.perm, v.n, B);
+      k_spmv<double, B, 0><<<g0(), NT, 0, s>>>(A0_, xi, nullptr, yi, nullptr, nullptr);
+      k_scatter_units<double, double><<<g, 256, 0, s>>>(yi, y_user, v.perm, v.n, B);
+    } else {
+      T* xi = static_cast<T*>(s_in);
+      T* yi = static_cast<T*>(s_out);
+      k_gather_units<T, double><<<g, 256, 0, s>>>(x_user, xi, v.perm, v.n, B);
+      k_spmv<T, B, 0><<<cdiv(v.nsl * SL, NT), NT, 0, s>>>(v.A(), xi, nullptr, yi, nullptr, nullptr);
+      k_scatter_units<double, T><<<g, 256, 0, s>>>(yi, y_user, v.perm, v.n, B);
+    }
+    AGG_CK(cudaGetLastError());
+    return AGG_OK;
+  }
+
   int sim_create(const SimParams& p, const double* mask_user, cudaStream_t s, std::string& err) override {
     if (sim_) { err = "a simulation already uses this hierarchy"; return AGG_EINVAL; }
     sp_ = p;
