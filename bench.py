@@ -37,7 +37,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="f32", choices=["f32", "f64", "bf16s"])
-    ap.add_argument("--n", type=int, default=512, help="elements per direction")
+    ap.add_argument("--workload", default="jsquare2d", choices=list(WORKLOADS))
+    ap.add_argument("--n", type=int, default=None, help="elements per direction (box workloads)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-kernel", type=int, default=None,
@@ -45,14 +46,30 @@ def parse():
     return ap.parse_args()
 
 
-def workload(n):
-    from paper_2602_16312_gb300 import workloads as W
-    return W.jittered_square_2d(n=n, degree=2, n_levels=4)
+WORKLOADS = {
+    # name: (constructor expression in workloads, default n)
+    "jsquare2d": ("W.jittered_square_2d(n={n}, degree=2, n_levels=4)", 512),
+    "jcube3d": ("W.jittered_cube_3d(n={n}, degree=2, n_levels=4, group=4)", 64),
+    "shell": ("W.ventricle_shell()", None),
+    "square2d": ("W.square_2d_fhn({n}, 1)", 16),
+}
+
+
+def workload_expr(args):
+    expr, n0 = WORKLOADS[args.workload]
+    return expr.format(n=args.n if args.n is not None else n0)
+
+
+def workload(args):
+    from paper_2602_16312_gb300 import workloads as W  # noqa: F401
+    return eval(workload_expr(args))
 
 
 def workload_name(wl):
-    return (f"{wl.name}: {wl.mesh.n_elements} quads, DG Q{wl.degree}, {wl.n_dofs} DoFs, "
-            f"{wl.n_levels} levels (<=16 per agglomerate), FHN, dt {wl.dt}, rtol {wl.rtol}")
+    cells = "quads" if wl.mesh.dim == 2 else "hexes"
+    model = "FHN" if wl.ionic["model"] == 0 else "Aliev-Panfilov"
+    return (f"{wl.name}: {wl.mesh.n_elements} {cells}, DG Q{wl.degree}, {wl.n_dofs} DoFs, "
+            f"{wl.n_levels} levels {[int(m.max()) + 1 for m in wl.maps]}, {model}, dt {wl.dt}, rtol {wl.rtol}")
 
 
 # ---------------------------------------------------------------- CPU oracle leg
@@ -62,7 +79,7 @@ sys.path.insert(0, {root!r})
 import numpy as np
 from paper_2602_16312_gb300 import workloads as W
 from oracle import sipg, multigrid as mg, monodomain as md
-wl = W.jittered_square_2d(n={n}, degree=2, n_levels=4)
+wl = {expr}
 disc = sipg.assemble(wl.mesh.vertices, wl.mesh.elements, wl.conductivity, wl.degree, wl.penalty_mode,
                      wl.penalty_coeff)
 opts = md.StepOptions(dt=wl.dt, ionic=wl.ionic, rtol=wl.rtol, iapp_value=wl.iapp_value, iapp_steps=wl.iapp_steps)
@@ -75,21 +92,21 @@ print(json.dumps(dict(t_step=t_step, iters=res.iterations)))
 """
 
 
-def cpu_oracle_sample(n):
+def cpu_oracle_sample(expr):
     """Runs the oracle single-threaded in a fresh process: one full time step
     (step 0: ionic update, RHS, PCG to 1e-8) of the benchmark workload, timed
     on this host's cores; the oracle's set-up is not timed."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, "-c", ORACLE_SNIPPET.format(root=ROOT, n=n)],
+    out = subprocess.run([sys.executable, "-c", ORACLE_SNIPPET.format(root=ROOT, expr=expr)],
                          env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, timeout=1800)
     if out.returncode != 0:
         raise RuntimeError("oracle leg failed: " + out.stderr.decode()[-2000:])
     return json.loads(out.stdout.decode().strip().splitlines()[-1])
 
 
-def cpu_baseline_entry(sample, n):
+def cpu_baseline_entry(sample, name):
     return {"value": 1.0 / sample["t_step"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"oracle (numpy/scipy float64, 1 thread) on the {n}x{n} Q2 workload: one full time "
+            "sample": (f"oracle (numpy/scipy float64, 1 thread) on {name}: one full time "
                        f"step (step 0: ionic update, RHS, PCG to 1e-8 in {sample['iters']} iterations) timed, "
                        f"{sample['t_step']:.1f} s; oracle set-up excluded")}
 
@@ -165,13 +182,13 @@ def run_ours(args, rank, world):
 
     sample = None
     if rank == 0 and not args.no_cpu_baseline:
-        sample = cpu_oracle_sample(args.n)   # before any GPU work
+        sample = cpu_oracle_sample(workload_expr(args))   # before any GPU work
 
     from paper_2602_16312_gb300 import aggmg, build
     build.build()
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
     dev = torch.device("cuda")
-    wl = workload(args.n)
+    wl = workload(args)
     t0 = time.time()
     mesh = aggmg.Mesh.from_workload(wl)
     hier = aggmg.Hierarchy(mesh, 1.0 / wl.dt, wl.maps, precision=args.form)
@@ -275,7 +292,7 @@ def run_ours(args, rank, world):
         "data": "synthetic",
         "mdof_per_s": N * total_steps / t / 1e6,
         "config": {"workload": workload_name(wl), "form": args.form, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (fine float64 matrix 0.85 GB, 129 MB L2)",
+                   "l2": f"inputs larger than L2 (fine float64 matrix {k0bytes / 1e9:.2f} GB, 129 MB L2)",
                    "levels": st["units"], "op_complexity": st["op_complexity"], "setup_s": setup_s,
                    "conditional_graph": os.environ.get("AGG_NO_COND_GRAPH") is None, "flexible_cg": flexible},
         "iterations": {"mean": float(np.mean(its)), "min": int(min(its)), "max": int(max(its)),
@@ -287,7 +304,7 @@ def run_ours(args, rank, world):
         "clocks": clk.summary(),
     }
     if sample is not None:
-        line["cpu_baseline"] = cpu_baseline_entry(sample, args.n)
+        line["cpu_baseline"] = cpu_baseline_entry(sample, wl.name)
     if rank == 0:
         print(json.dumps(line), flush=True)
     sim.close()
@@ -298,10 +315,9 @@ def run_reference(args, rank):
     """The oracle as it stands, on the host cores, as the reference arm."""
     if rank != 0:
         return
-    sample = cpu_oracle_sample(args.n)
-    base = cpu_baseline_entry(sample, args.n)
-    from paper_2602_16312_gb300 import workloads as W
-    wl = W.jittered_square_2d(n=args.n, degree=2, n_levels=4)
+    sample = cpu_oracle_sample(workload_expr(args))
+    wl = workload(args)
+    base = cpu_baseline_entry(sample, wl.name)
     line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sample["t_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",

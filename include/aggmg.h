@@ -78,6 +78,10 @@ typedef struct {
   int penalty_mode;             /* 0 or 1, see above                             */
   double penalty_coeff;
   int quad_extra;               /* >= 0; 1 gives p+2 points per direction        */
+  int adjoint_data;             /* 1: also keep the per-element parts of A that
+                                   the adjoint's conductivity gradient needs
+                                   (volume form + 4 face blocks per neighbour;
+                                   about 5x the stiffness memory)              */
 } agg_mesh_desc;
 
 /* Assembles, on the host in float64, the SIPG stiffness A and the element
@@ -87,6 +91,12 @@ agg_status agg_dg_mesh_create(const agg_mesh_desc* desc, agg_mesh_t* out);
 agg_status agg_dg_mesh_destroy(agg_mesh_t mesh);
 /* n_dofs = n_elements * (p+1)^dim; n_faces = number of interior faces. */
 agg_status agg_dg_mesh_info(agg_mesh_t mesh, int64_t* n_dofs, int64_t* n_faces);
+/* Point evaluation of DG functions (sensors): for each of n host points
+ * [n][dim], the containing element (Newton inversion of the element map) and
+ * the B basis values there, so u_h(x_s) = sum_i weights[s][i] u[elem[s]*B+i].
+ * Host arrays. AGG_EINVAL if a point lies outside the mesh. */
+agg_status agg_dg_mesh_locate(agg_mesh_t mesh, int64_t n, const double* points, int64_t* elem,
+                              double* weights);
 
 /* ------------------------------------------------------------------ hierarchy */
 enum { AGG_F64 = 0, AGG_F32 = 1, AGG_F32_BF16SMOOTH = 2 };
@@ -215,6 +225,23 @@ agg_status agg_monodomain_create(agg_hier_t hier, const agg_sim_opts* opts, agg_
 agg_status agg_monodomain_step(agg_sim_t sim, int n_steps, double* u_dev, double* w_dev,
                                int* iters_out, void* stream);
 agg_status agg_monodomain_set_clock(agg_sim_t sim, int64_t step);
+/* Discrete adjoint of one step n -> n+1 (not in the paper; the reverse of
+ * agg_monodomain_step for gradients of a loss of the states). Inputs: the
+ * states u_n, w_n at the start of the step and u_np1 after it; ubar, wbar =
+ * dL/du^{n+1}, dL/dw^{n+1} on entry, overwritten with dL/du^n, dL/dw^n:
+ *   lambda = K^{-1} ubar (same MG-PCG and options as the forward solve,
+ *   zero initial guess, K = c M + A symmetric), q = M lambda,
+ *   w~ = wbar - chi I_w(u^n, w^{n+1}) q,
+ *   ubar <- q (c - chi I_u(u^n, w^{n+1})) + dt H_u(u^n, w^n) w~,
+ *   wbar <- w~ (1 + dt H_w(u^n, w^n)).
+ * grad_logD_dev [n_elements] accumulates, per element e, the derivative of L
+ * with respect to log s_e for D_e -> s_e D_e: -lambda^T A_e u^{n+1}, A_e the
+ * part of A built with D_e (element-local volume form and e's share of its
+ * face forms). Needs a mesh created with adjoint_data = 1. Synchronises
+ * `stream`; returns the adjoint solve's status. */
+agg_status agg_monodomain_adjoint_step(agg_sim_t sim, const double* u_n_dev, const double* w_n_dev,
+                                       const double* u_np1_dev, double* ubar_dev, double* wbar_dev,
+                                       double* grad_logD_dev, void* stream);
 agg_status agg_monodomain_destroy(agg_sim_t sim);
 
 /* ------------------------------------------------------------------ instrumentation
@@ -235,7 +262,11 @@ agg_status agg_kernel_cost(agg_hier_t hier, int kernel, double* bytes, double* f
  * agg_dg_mesh_copy `what`: 0 stiffness row pointers (int64, n_elements+1),
  * 1 block columns (int32, nnzb), 2 blocks (float64, nnzb*B*B, row-major
  * blocks), 3 element mass blocks (float64, n_elements*B*B), 4 element
- * volumes (float64, n_elements). The stiffness excludes the mass term. */
+ * volumes (float64, n_elements), 5 element volume forms (float64,
+ * n_elements*B*B) and 6 per-block face parts (float64, nnzb*4*B*B: for block
+ * k of row e with column n, the (ee, en, ne, nn) blocks of the face terms
+ * built with D_e), both only with adjoint_data. The stiffness excludes the
+ * mass term. */
 agg_status agg_dg_mesh_copy(agg_mesh_t mesh, int what, void* dst);
 agg_status agg_dg_mesh_nnzb(agg_mesh_t mesh, int64_t* nnzb);
 

@@ -14,6 +14,17 @@ the BDF2 history replaced by one level): mass coefficient c = chi C_m / dt of
 A0 = c M + A, U* = u^n, b = M (c u^n + f). The paper's BDF2 with the
 extrapolation U* = 2u^n - u^{n-1} is not part of this oracle.
 
+Adjoint (not in the paper): the discrete adjoint of this recurrence. With
+K = c M + A, a reverse step n+1 -> n takes ubar = dL/du^{n+1},
+wbar = dL/dw^{n+1} and returns their values at step n and the per-element
+log-conductivity gradient gamma_e = -lambda^T A_e u^{n+1} (A_e: part of A
+built with D_e, see sipg.attributed_forms):
+  lambda = K^{-1} ubar,  q = M lambda,
+  wt = wbar - chi I_w(u^n, w^{n+1}) q,
+  ubar_n = q (c - chi I_u(u^n, w^{n+1})) + dt H_u(u^n, w^n) wt,
+  wbar_n = wt (1 + dt H_w(u^n, w^n)).
+Pinned by central finite differences of the loss (tests).
+
 Readings: the ionic ODE uses forward Euler (the workloads' "explicit
 update"; the paper integrates it with BDF2). FitzHugh-Nagumo follows
 Section 2.3.1 with k = 1, Gamma = b. Aliev-Panfilov is not in the paper; its
@@ -111,3 +122,42 @@ def run(disc, hier, opts: StepOptions, u0, w0, mask, n_steps):
         u, w, res = step(disc, hier, opts, u, w, mask, n)
         its.append(res.iterations)
     return u, w, its
+
+
+def adjoint_step(disc, hier, opts: StepOptions, forms, u_n, w_n, u_np1, ubar, wbar, rtol=1e-12):
+    """Reverse of step(): returns (ubar_n, wbar_n, gamma)."""
+    prm, dt, chi = opts.ionic, opts.dt, opts.chi
+    c = opts.mass_coeff()
+    _, H = ionic(prm, u_n, w_n)
+    w_np1 = w_n + dt * H
+    res = pcg(hier.levels[0].A, ubar, np.zeros_like(ubar), lambda r: vcycle(hier, r), rtol, 10 * opts.max_it)
+    lam = res.x
+    q = disc.M @ lam
+    I_u, I_w, _, _ = ionic_jacobian(prm, u_n, w_np1)
+    _, _, H_u, H_w = ionic_jacobian(prm, u_n, w_n)
+    wt = wbar - chi * I_w * q
+    ubar_n = q * (c - chi * I_u) + dt * H_u * wt
+    wbar_n = wt * (1.0 + dt * H_w)
+    from .sipg import attributed_bilinear
+    gamma = -attributed_bilinear(forms, lam, u_np1, disc.B)
+    return ubar_n, wbar_n, gamma
+
+
+def trajectory(disc, hier, opts: StepOptions, u0, w0, mask, n_steps):
+    """States u^0..u^N, w^0..w^N of run()."""
+    us, ws = [u0.copy()], [w0.copy()]
+    for n in range(n_steps):
+        u, w, _ = step(disc, hier, opts, us[-1], ws[-1], mask, n)
+        us.append(u)
+        ws.append(w)
+    return us, ws
+
+
+def gradient_log_conductivity(disc, hier, opts: StepOptions, forms, us, ws, ubar_N, rtol=1e-12):
+    """dL/d(log s_e) for a loss with dL/du^N = ubar_N (and no w^N term)."""
+    ubar, wbar = ubar_N.copy(), np.zeros_like(ubar_N)
+    gamma = np.zeros(disc.n_elements)
+    for n in range(len(us) - 2, -1, -1):
+        ubar, wbar, g = adjoint_step(disc, hier, opts, forms, us[n], ws[n], us[n + 1], ubar, wbar, rtol)
+        gamma += g
+    return gamma, ubar, wbar

@@ -166,7 +166,7 @@ def find_faces(elements, dim):
     return ep, fp, em, fm, match
 
 
-def face_matrices(vertices, elements, D, p, volumes, c_pen, quad_extra=1, chunk=65536):
+def face_matrices(vertices, elements, D, p, volumes, c_pen, quad_extra=1, chunk=65536, side=None):
     """Face blocks of the SIPG form on every interior face.
 
     Returns (ep, em, blocks) with blocks (F, 2, 2, B, B): blocks[F, si, sj] is
@@ -175,7 +175,10 @@ def face_matrices(vertices, elements, D, p, volumes, c_pen, quad_extra=1, chunk=
                        -1/2 sgn_j phi_j (D_si grad phi_i . n)
                        + sigma_q sgn_i sgn_j phi_i phi_j ]
     with n the unit outward normal of the + element, sgn(+) = 1, sgn(-) = -1,
-    sigma_q = c_pen max(|F|/|K+|, |F|/|K-|) n^T ((D+ + D-)/2) n."""
+    sigma_q = c_pen max(|F|/|K+|, |F|/|K-|) n^T ((D+ + D-)/2) n.
+
+    side = 0 (1) keeps only the terms built with D+ (D-): the blocks are linear
+    in (D+, D-) jointly, so the two parts add up to the full face blocks."""
     dim = vertices.shape[1]
     q = p + 1 + quad_extra
     x1, w1 = re.gauss_rule(q)
@@ -220,6 +223,10 @@ def face_matrices(vertices, elements, D, p, volumes, c_pen, quad_extra=1, chunk=
         alpha = c_pen * np.maximum(area / volumes[ep[sl]], area / volumes[em[sl]])
         Dp = D[ep[sl]]
         Dm = D[em[sl]]
+        if side == 0:
+            Dm = np.zeros_like(Dm)
+        elif side == 1:
+            Dp = np.zeros_like(Dp)
         Dbar = 0.5 * (Dp + Dm)
         sigma = alpha[:, None] * np.einsum("fqk,fkm,fqm->fq", n, Dbar, n)
         phi_p, gh_p = re.tensor_basis(p, dim, pts_p)
@@ -292,3 +299,70 @@ def nodal_points(vertices, elements, p):
     xi = re.tensor_points(re.gll_nodes(p), dim)
     N, _ = re.multilinear_shape(dim, xi)
     return np.einsum("iv,evk->eik", N, vertices[elements])
+
+
+def attributed_forms(vertices, elements, D, p, penalty_mode=0, penalty_coeff=10.0, quad_extra=1):
+    """Split of the SIPG stiffness into per-element parts, A = sum_e A_e:
+    A_e is the volume form of e plus, on each interior face of e, the face
+    terms built with D_e (consistency terms of e's side, half the penalty).
+    Returns (Ke, ep, em, Yp, Ym) with Yp/Ym (F, 2, 2, B, B) the face blocks
+    attributed to the + and - element. A_e is the derivative of A with respect
+    to a scale factor s_e of D_e, at s_e = 1 (A is linear in each D_e)."""
+    vertices = np.asarray(vertices, dtype=np.float64)
+    elements = np.asarray(elements, dtype=np.int64)
+    D = np.asarray(D, dtype=np.float64)
+    Me, Ke, vol = volume_matrices(vertices, elements, D, p, quad_extra)
+    c_pen = penalty_constant(p, penalty_mode, penalty_coeff)
+    ep, em, Yp = face_matrices(vertices, elements, D, p, vol, c_pen, quad_extra, side=0)
+    _, _, Ym = face_matrices(vertices, elements, D, p, vol, c_pen, quad_extra, side=1)
+    return Ke, ep, em, Yp, Ym
+
+
+def attributed_bilinear(forms, lam, u, B):
+    """g_e = lam^T A_e u for every element (forms from attributed_forms)."""
+    Ke, ep, em, Yp, Ym = forms
+    E = Ke.shape[0]
+    L = lam.reshape(E, B)
+    U = u.reshape(E, B)
+    g = np.einsum("ei,eij,ej->e", L, Ke, U)
+    for Y, owner in ((Yp, ep), (Ym, em)):
+        val = (np.einsum("fi,fij,fj->f", L[ep], Y[:, 0, 0], U[ep])
+               + np.einsum("fi,fij,fj->f", L[ep], Y[:, 0, 1], U[em])
+               + np.einsum("fi,fij,fj->f", L[em], Y[:, 1, 0], U[ep])
+               + np.einsum("fi,fij,fj->f", L[em], Y[:, 1, 1], U[em]))
+        np.add.at(g, owner, val)
+    return g
+
+
+def locate_points(vertices, elements, p, points, tol=1e-12):
+    """Element and reference coordinates of each point (Newton on the
+    multilinear map, among elements whose vertex box contains the point), and
+    the interpolation weights phi_i(xi) of its element: returns (elem, W) with
+    u_h(point) = sum_i W[s, i] u[elem[s]*B + i]."""
+    dim = vertices.shape[1]
+    X = vertices[elements]
+    lo, hi = X.min(axis=1), X.max(axis=1)
+    elem = np.empty(len(points), dtype=np.int64)
+    xis = np.empty((len(points), dim))
+    for s, x in enumerate(points):
+        cand = np.nonzero(np.all((lo - 1e-12 <= x) & (x <= hi + 1e-12), axis=1))[0]
+        found = False
+        for e in cand:
+            xi = np.full(dim, 0.5)
+            for _ in range(50):
+                N, dN = re.multilinear_shape(dim, xi[None])
+                r = N[0] @ X[e] - x
+                J = np.einsum("vl,vk->kl", dN[0], X[e])
+                step = np.linalg.solve(J, r)
+                xi = xi - step
+                if np.max(np.abs(step)) < 1e-15:
+                    break
+            if np.all(xi >= -1e-10) and np.all(xi <= 1 + 1e-10):
+                elem[s] = e
+                xis[s] = np.clip(xi, 0.0, 1.0)
+                found = True
+                break
+        if not found:
+            raise ValueError(f"point {s} is outside the mesh")
+    phi, _ = re.tensor_basis(p, dim, xis)
+    return elem, phi.T

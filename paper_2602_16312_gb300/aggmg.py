@@ -32,7 +32,7 @@ class MeshDesc(C.Structure):
     _fields_ = [("dim", C.c_int), ("degree", C.c_int), ("n_vertices", C.c_int64), ("n_elements", C.c_int64),
                 ("vertices", C.POINTER(C.c_double)), ("elements", C.POINTER(C.c_int64)),
                 ("conductivity", C.POINTER(C.c_double)), ("penalty_mode", C.c_int),
-                ("penalty_coeff", C.c_double), ("quad_extra", C.c_int)]
+                ("penalty_coeff", C.c_double), ("quad_extra", C.c_int), ("adjoint_data", C.c_int)]
 
 
 class MGOpts(C.Structure):
@@ -67,6 +67,9 @@ _SIGS = {
     "agg_dg_mesh_destroy": [C.c_void_p],
     "agg_dg_mesh_info": [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     "agg_dg_mesh_nnzb": [C.c_void_p, C.POINTER(C.c_int64)],
+    "agg_dg_mesh_locate": [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
+    "agg_monodomain_adjoint_step": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_void_p],
     "agg_dg_mesh_copy": [C.c_void_p, C.c_int, C.c_void_p],
     "agg_mg_opts_default": [C.POINTER(MGOpts)],
     "agg_mg_hierarchy_setup": [C.c_void_p, C.c_double, C.POINTER(MGOpts), C.c_void_p, C.POINTER(C.c_void_p)],
@@ -145,7 +148,7 @@ class Mesh:
     """agg_dg_mesh_create: SIPG stiffness and element mass blocks (host FP64)."""
 
     def __init__(self, vertices, elements, conductivity, degree, penalty_mode=1, penalty_coeff=10.0,
-                 quad_extra=1):
+                 quad_extra=1, adjoint_data=False):
         self.vertices = np.ascontiguousarray(vertices, dtype=np.float64)
         self.elements = np.ascontiguousarray(elements, dtype=np.int64)
         self.conductivity = np.ascontiguousarray(conductivity, dtype=np.float64)
@@ -157,15 +160,24 @@ class Mesh:
                      self.vertices.ctypes.data_as(C.POINTER(C.c_double)),
                      self.elements.ctypes.data_as(C.POINTER(C.c_int64)),
                      self.conductivity.ctypes.data_as(C.POINTER(C.c_double)),
-                     penalty_mode, penalty_coeff, quad_extra)
+                     penalty_mode, penalty_coeff, quad_extra, int(adjoint_data))
         h = C.c_void_p()
         _check(lib().agg_dg_mesh_create(C.byref(d), C.byref(h)))
         self.handle = h
 
     @classmethod
-    def from_workload(cls, wl):
-        return cls(wl.mesh.vertices, wl.mesh.elements, wl.conductivity, wl.degree, wl.penalty_mode,
-                   wl.penalty_coeff)
+    def from_workload(cls, wl, conductivity=None, adjoint_data=False):
+        D = wl.conductivity if conductivity is None else conductivity
+        return cls(wl.mesh.vertices, wl.mesh.elements, D, wl.degree, wl.penalty_mode, wl.penalty_coeff,
+                   adjoint_data=adjoint_data)
+
+    def locate(self, points):
+        """(elem, weights) of agg_dg_mesh_locate for host points (n, dim)."""
+        pts = np.ascontiguousarray(points, dtype=np.float64)
+        elem = np.empty(len(pts), np.int64)
+        w = np.empty((len(pts), self.B), np.float64)
+        _check(lib().agg_dg_mesh_locate(self.handle, len(pts), pts.ctypes.data, elem.ctypes.data, w.ctypes.data))
+        return elem, w
 
     @property
     def n_dofs(self):
@@ -191,6 +203,16 @@ class Mesh:
         out = np.empty((self.n_elements, self.B, self.B))
         _check(lib().agg_dg_mesh_copy(self.handle, 3, out.ctypes.data))
         return out
+
+    def adjoint_forms(self):
+        """(Ke (E,B,B), Y (nnzb,4,B,B)) of a mesh made with adjoint_data."""
+        nnzb = C.c_int64()
+        _check(lib().agg_dg_mesh_nnzb(self.handle, C.byref(nnzb)))
+        Ke = np.empty((self.n_elements, self.B, self.B))
+        Y = np.empty((nnzb.value, 4, self.B, self.B))
+        _check(lib().agg_dg_mesh_copy(self.handle, 5, Ke.ctypes.data))
+        _check(lib().agg_dg_mesh_copy(self.handle, 6, Y.ctypes.data))
+        return Ke, Y
 
     def volumes(self):
         out = np.empty(self.n_elements)
@@ -363,6 +385,13 @@ class Monodomain:
 
     def set_clock(self, step):
         _check(lib().agg_monodomain_set_clock(self.handle, step))
+
+    def adjoint_step(self, u_n, w_n, u_np1, ubar, wbar, grad_logD, stream=None):
+        """agg_monodomain_adjoint_step: ubar, wbar updated in place, grad_logD accumulated."""
+        _check(lib().agg_monodomain_adjoint_step(self.handle, C.c_void_p(_dptr(u_n)), C.c_void_p(_dptr(w_n)),
+                                                 C.c_void_p(_dptr(u_np1)), C.c_void_p(_dptr(ubar)),
+                                                 C.c_void_p(_dptr(wbar)), C.c_void_p(_dptr(grad_logD)),
+                                                 C.c_void_p(_stream(stream))))
 
     def close(self):
         if self.handle:

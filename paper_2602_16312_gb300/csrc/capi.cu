@@ -105,6 +105,7 @@ agg_status agg_dg_mesh_create(const agg_mesh_desc* d, agg_mesh_t* out) {
     m.penalty_mode = d->penalty_mode;
     m.penalty_coeff = d->penalty_coeff;
     m.quad_extra = d->quad_extra;
+    m.adjoint_data = d->adjoint_data != 0;
     std::string err;
     int s = mesh_build(m, err);
     if (s) return fail((agg_status)s, err);
@@ -127,6 +128,14 @@ agg_status agg_dg_mesh_info(agg_mesh_t m, int64_t* n_dofs, int64_t* n_faces) {
   return AGG_OK;
 }
 
+agg_status agg_dg_mesh_locate(agg_mesh_t mh, int64_t n, const double* pts, int64_t* elem, double* weights) {
+  if (!mh || n < 0 || (n > 0 && (!pts || !elem || !weights))) return fail(AGG_EINVAL, "bad argument");
+  std::string err;
+  int rc = mesh_locate(mh->m, n, pts, elem, weights, err);
+  if (rc) return fail((agg_status)rc, err);
+  return AGG_OK;
+}
+
 agg_status agg_dg_mesh_nnzb(agg_mesh_t m, int64_t* nnzb) {
   if (!m || !nnzb) return fail(AGG_EINVAL, "NULL argument");
   *nnzb = m->m.A.nnzb();
@@ -142,6 +151,12 @@ agg_status agg_dg_mesh_copy(agg_mesh_t mh, int what, void* dst) {
     case 2: std::memcpy(dst, m.A.val.data(), sizeof(double) * m.A.val.size()); break;
     case 3: std::memcpy(dst, m.Me.data(), sizeof(double) * m.Me.size()); break;
     case 4: std::memcpy(dst, m.vol.data(), sizeof(double) * m.vol.size()); break;
+    case 5:
+    case 6:
+      if (!m.adjoint_data) return fail(AGG_EINVAL, "mesh has no adjoint data");
+      if (what == 5) std::memcpy(dst, m.Ke.data(), sizeof(double) * m.Ke.size());
+      else std::memcpy(dst, m.Y.data(), sizeof(double) * m.Y.size());
+      break;
     default: return fail(AGG_EINVAL, "what");
   }
   return AGG_OK;
@@ -436,6 +451,19 @@ agg_status agg_profile_kernel(agg_hier_t h, int kernel, int reps, void* stream) 
 agg_status agg_kernel_cost(agg_hier_t h, int kernel, double* bytes, double* flops) {
   if (!h || !bytes || !flops) return fail(AGG_EINVAL, "NULL argument");
   if (h->eng->kernel_cost(kernel, *bytes, *flops)) return fail(AGG_EINVAL, "unknown kernel id");
+  return AGG_OK;
+}
+
+agg_status agg_monodomain_adjoint_step(agg_sim_t sim, const double* u_n, const double* w_n, const double* u_np1,
+                                       double* ubar, double* wbar, double* grad, void* stream) {
+  if (!sim || !u_n || !w_n || !u_np1 || !ubar || !wbar || !grad) return fail(AGG_EINVAL, "NULL argument");
+  agg_status s = check_device(sim->h);
+  if (s) return s;
+  std::string err;
+  SolveResult r;
+  int rc = sim->h->eng->adjoint_step(u_n, w_n, u_np1, ubar, wbar, grad, r, (cudaStream_t)stream, err);
+  if (rc) return fail((agg_status)rc, err);
+  if (r.status) return fail((agg_status)r.status, std::string("adjoint solve: ") + agg_status_string(r.status));
   return AGG_OK;
 }
 

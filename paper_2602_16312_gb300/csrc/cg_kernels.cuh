@@ -249,6 +249,108 @@ static __global__ void __launch_bounds__(NT) k_ionic_rhs(const double* __restric
   for (int r = 0; r < B; ++r) b[o + r] = acc[r];
 }
 
+// Partial derivatives of the ionic model at one DoF (I_u, I_w, H_u, H_w).
+__device__ __forceinline__ void ionic_jac(const IonicParams& p, double u, double w, double& Iu, double& Iw,
+                                          double& Hu, double& Hw) {
+  const double dcub = p.k * (3.0 * u * u - 2.0 * (p.a + 1.0) * u + p.a);
+  if (p.model == 0) {
+    Iu = dcub;
+    Iw = 1.0;
+    Hu = p.eps;
+    Hw = -p.eps * p.gamma;
+  } else {
+    Iu = dcub + w;
+    Iw = u;
+    const double den = u + p.mu2;
+    const double e = p.eps + p.mu1 * w / den;
+    const double g = -w - p.k * u * (u - p.a - 1.0);
+    const double e_u = -p.mu1 * w / (den * den), e_w = p.mu1 / den;
+    const double g_u = -p.k * (2.0 * u - p.a - 1.0);
+    Hu = e_u * g + e * g_u;
+    Hw = e_w * g - e;
+  }
+}
+
+// Reverse of one time step, pointwise part, for the thread's element
+// (discrete adjoint of the step; lambda = K^{-1} ubar is the input):
+//   q = M_e lambda_e,  w~ = wbar - chi I_w(u_n, w_np1) q,
+//   ubar_n = q (c - chi I_u(u_n, w_np1)) + dt H_u(u_n, w_n) w~,
+//   wbar_n = w~ (1 + dt H_w(u_n, w_n)),   with w_np1 = w_n + dt H(u_n, w_n).
+template <int B>
+static __global__ void __launch_bounds__(NT) k_adj_pointwise(const double* __restrict__ Me, const double* __restrict__ lam,
+                                                             const double* __restrict__ u_n, const double* __restrict__ w_n,
+                                                             double* __restrict__ ubar, double* __restrict__ wbar,
+                                                             IonicParams prm, double dt, double chi, double c,
+                                                             int64_t nslices) {
+  constexpr int KP = Pad<double, B>::KP;
+  const int64_t unit = (int64_t)blockIdx.x * NT + threadIdx.x;
+  const int64_t slice = unit / SL;
+  const int lane = threadIdx.x & 31;
+  if (slice >= nslices) return;
+  const size_t o = (size_t)unit * B;
+  double lv[B], q[B];
+#pragma unroll
+  for (int r = 0; r < B; ++r) { lv[r] = lam[o + r]; q[r] = 0.0; }
+  block_mv<double, double, B>(Me + (size_t)slice * SL * KP, lane, lv, q);
+#pragma unroll
+  for (int r = 0; r < B; ++r) {
+    const double un = u_n[o + r], wn = w_n[o + r];
+    double I, H, Iu, Iw, Hu, Hw, Iu1, Iw1, Hu1, Hw1;
+    ionic_eval(prm, un, wn, I, H);
+    const double w1 = wn + dt * H;
+    ionic_jac(prm, un, w1, Iu1, Iw1, Hu1, Hw1);
+    ionic_jac(prm, un, wn, Iu, Iw, Hu, Hw);
+    const double wt = wbar[o + r] - chi * Iw1 * q[r];
+    ubar[o + r] = q[r] * (c - chi * Iu1) + dt * Hu * wt;
+    wbar[o + r] = wt * (1.0 + dt * Hw);
+  }
+}
+
+// Per-element log-conductivity gradient, accumulated in the caller's order:
+//   grad[e] -= lam_e^T Ke u_e + sum_faces [lam_e; lam_n]^T Y_e,F [u_e; u_n]
+// with Ke the volume form and Y_e,F the face terms built with D_e (four
+// sliced blocks per stiffness slot, in the slot order of the fine operator).
+template <int B>
+static __global__ void __launch_bounds__(NT) k_grad_logD(SellView<double> A, const double* __restrict__ Ke,
+                                                         const double* __restrict__ Y, const double* __restrict__ lam,
+                                                         const double* __restrict__ u, const int64_t* __restrict__ perm,
+                                                         double* __restrict__ grad, int64_t n) {
+  constexpr int KP = Pad<double, B>::KP;
+  const int64_t unit = (int64_t)blockIdx.x * NT + threadIdx.x;
+  const int64_t slice = unit / SL;
+  const int lane = threadIdx.x & 31;
+  if (slice >= A.nslices) return;
+  const size_t o = (size_t)unit * B;
+  double le[B], ue[B], t[B];
+#pragma unroll
+  for (int r = 0; r < B; ++r) { le[r] = lam[o + r]; ue[r] = u[o + r]; t[r] = 0.0; }
+  block_mv<double, double, B>(Ke + (size_t)slice * SL * KP, lane, ue, t);
+  double g = 0.0;
+#pragma unroll
+  for (int r = 0; r < B; ++r) g += le[r] * t[r];
+  const int s0 = A.slice_ptr[slice], s1 = A.slice_ptr[slice + 1];
+  for (int j = s0; j < s1; ++j) {
+    const int col = A.cols[(size_t)j * SL + lane];
+    if (col == unit) continue;                 // diagonal or padding slot
+    double ln[B], un[B], t1[B], t2[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+      ln[r] = lam[(size_t)col * B + r];
+      un[r] = u[(size_t)col * B + r];
+      t1[r] = 0.0;
+      t2[r] = 0.0;
+    }
+    const double* Yj = Y + (size_t)j * 4 * SL * KP;
+    block_mv<double, double, B>(Yj, lane, ue, t1);
+    block_mv<double, double, B>(Yj + (size_t)SL * KP, lane, un, t1);
+    block_mv<double, double, B>(Yj + (size_t)2 * SL * KP, lane, ue, t2);
+    block_mv<double, double, B>(Yj + (size_t)3 * SL * KP, lane, un, t2);
+#pragma unroll
+    for (int r = 0; r < B; ++r) g += le[r] * t1[r] + ln[r] * t2[r];
+  }
+  if (unit < n) grad[perm[unit]] -= g;
+}
+
 // end of a time step: record the iteration count, advance the clock
 static __global__ void k_step_end(const CGState* st, int64_t* step, int* iters, int* slot, int capacity, int* status) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {

@@ -43,6 +43,9 @@ class EngineBase {
   virtual int sim_step(int n_steps, double* u_user, double* w_user, int* iters_host, int64_t& clock,
                        cudaStream_t s, std::string& err) = 0;
   virtual int sim_destroy() = 0;
+  // one reverse time step (discrete adjoint), vectors in the caller's order
+  virtual int adjoint_step(const double* u_n, const double* w_n, const double* u_np1, double* ubar, double* wbar,
+                           double* grad, SolveResult& res, cudaStream_t s, std::string& err) = 0;
   virtual bool uses_conditional_graph() const = 0;
   // instrumentation: launch one hot kernel `reps` times on the internal
   // buffers, and its algorithmic bytes / flops per launch

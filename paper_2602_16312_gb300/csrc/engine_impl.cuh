@@ -84,6 +84,9 @@ class Engine : public EngineBase {
   int64_t* step_ = nullptr;
   int *iters_ = nullptr, *slot_ = nullptr, *sim_status_ = nullptr;
   int cap_ = 1024;
+  // adjoint data and buffers
+  double *Ke_ = nullptr, *Y_ = nullptr;
+  double *ua_ = nullptr, *wa_ = nullptr, *ub_ = nullptr, *wb_ = nullptr;
   cudaGraphExec_t step_exec_ = nullptr, step_pro_exec_ = nullptr, step_epi_exec_ = nullptr;
 
   template <typename X>
@@ -384,6 +387,37 @@ class Engine : public EngineBase {
         std::memcpy(&me[(size_t)r * B * B], &m.Me[(size_t)h.lev[0].perm[r] * B * B], sizeof(double) * B * B);
       if ((rc = upload_blocks<double>(me, m.ne, lev_[0].nsl, &Me_, err))) return rc;
     }
+    // adjoint data: volume forms and per-slot face parts in the fine operator's slot order
+    if (m.adjoint_data) {
+      const HostLevel& l0 = h.lev[0];
+      std::vector<double> ke((size_t)m.ne * B * B);
+      for (int64_t r = 0; r < m.ne; ++r)
+        std::memcpy(&ke[(size_t)r * B * B], &m.Ke[(size_t)l0.perm[r] * B * B], sizeof(double) * B * B);
+      if ((rc = upload_blocks<double>(ke, m.ne, lev_[0].nsl, &Ke_, err))) return rc;
+      constexpr int KP = Pad<double, B>::KP;
+      const int64_t nsl = lev_[0].nsl;
+      std::vector<int64_t> sp(nsl + 1, 0);
+      for (int64_t sl = 0; sl < nsl; ++sl) {
+        int64_t mx = 1;
+        for (int64_t u = sl * SL; u < std::min<int64_t>(m.ne, (sl + 1) * SL); ++u)
+          mx = std::max<int64_t>(mx, l0.A.rowptr[u + 1] - l0.A.rowptr[u]);
+        sp[sl + 1] = sp[sl] + mx;
+      }
+      std::vector<double> hy((size_t)sp[nsl] * 4 * SL * KP, 0.0);
+      for (int64_t r = 0; r < m.ne; ++r) {
+        const int64_t e = l0.perm[r];
+        std::vector<std::pair<int64_t, int64_t>> cols;
+        for (int64_t k = m.A.rowptr[e]; k < m.A.rowptr[e + 1]; ++k) cols.push_back({l0.inv[m.A.col[k]], k});
+        std::sort(cols.begin(), cols.end());
+        for (size_t j = 0; j < cols.size(); ++j) {
+          const int64_t slot = sp[r / SL] + (int64_t)j;
+          for (int b = 0; b < 4; ++b)
+            pack<double>(&m.Y[((size_t)cols[j].second * 4 + b) * B * B], &hy[((size_t)slot * 4 + b) * SL * KP],
+                         (int)(r % SL));
+        }
+      }
+      if ((rc = upload(&Y_, hy.data(), hy.size(), err))) return rc;
+    }
     // coarsest: inverse Cholesky factor and its transpose
     nc_ = h.nc;
     {
@@ -604,6 +638,43 @@ class Engine : public EngineBase {
       case 3: bytes = n0 * bb * sT + 2 * N * sT + (double)lev_[1].n * B * sT + n0 * 4; flops = 2 * n0 * bb + N; break;
       default: return AGG_EINVAL;
     }
+    return AGG_OK;
+  }
+
+  int adjoint_step(const double* u_n, const double* w_n, const double* u_np1, double* ubar, double* wbar,
+                   double* grad, SolveResult& res, cudaStream_t s, std::string& err) override {
+    if (!sim_) { err = "no simulation"; return AGG_EINVAL; }
+    if (!Ke_ || !Y_) { err = "the mesh was created without adjoint data (agg_mesh_desc.adjoint_data)"; return AGG_EINVAL; }
+    int rc;
+    const int64_t N = N0();
+    if (!ua_) {
+      for (double** pp : {&ua_, &wa_, &ub_, &wb_})
+        if ((rc = dalloc(pp, N, err))) return rc;
+    }
+    const Lev& v0 = lev_[0];
+    const int64_t g = cdiv(v0.n * B, 256);
+    // lambda = K^{-1} ubar by the same MG-PCG, from a zero guess
+    k_gather_units<double, double><<<g, 256, 0, s>>>(ubar, b_, v0.perm, v0.n, B);
+    AGG_CK(cudaMemsetAsync(x_, 0, sizeof(double) * N, s));
+    k_set_opts<<<1, 1, 0, s>>>(st_, sp_.pcg.rtol, sp_.pcg.atol, sp_.pcg.max_it, sp_.pcg.flexible);
+    if ((rc = run_solve(solve_exec_, init_exec_, nullptr, s, err))) return rc;
+    k_gather_units<double, double><<<g, 256, 0, s>>>(u_n, ua_, v0.perm, v0.n, B);
+    k_gather_units<double, double><<<g, 256, 0, s>>>(w_n, wa_, v0.perm, v0.n, B);
+    k_gather_units<double, double><<<g, 256, 0, s>>>(u_np1, ub_, v0.perm, v0.n, B);
+    k_gather_units<double, double><<<g, 256, 0, s>>>(wbar, wb_, v0.perm, v0.n, B);
+    IonicParams ip{sp_.model, sp_.k, sp_.a, sp_.eps, sp_.gamma, sp_.mu1, sp_.mu2};
+    const double c = sp_.chi * sp_.cm / sp_.dt;
+    k_adj_pointwise<B><<<g0(), NT, 0, s>>>(Me_, x_, ua_, wa_, b_, wb_, ip, sp_.dt, sp_.chi, c, v0.nsl);
+    k_grad_logD<B><<<g0(), NT, 0, s>>>(A0_, Ke_, Y_, x_, ub_, v0.perm, grad, v0.n);
+    k_scatter_units<double, double><<<g, 256, 0, s>>>(b_, ubar, v0.perm, v0.n, B);
+    k_scatter_units<double, double><<<g, 256, 0, s>>>(wb_, wbar, v0.perm, v0.n, B);
+    AGG_CK(cudaMemcpyAsync(st_host_, st_, sizeof(CGState), cudaMemcpyDeviceToHost, s));
+    AGG_CK(cudaStreamSynchronize(s));
+    AGG_CK(cudaGetLastError());
+    res.iterations = st_host_->iter;
+    res.r0 = st_host_->r0;
+    res.rn = std::sqrt(st_host_->rr);
+    res.status = st_host_->status;
     return AGG_OK;
   }
 

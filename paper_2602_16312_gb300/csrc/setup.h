@@ -42,7 +42,17 @@ struct Mesh {
   std::vector<double> Me;        // [ne][B][B] element mass blocks
   std::vector<double> vol;       // [ne]
   int64_t n_faces = 0;           // interior faces
+  // adjoint data (when adjoint_data): per stiffness block k of row e with
+  // column n != e, the four blocks (ee, en, ne, nn) of the face terms built
+  // with D_e; with Ke the volume form, sum_e of these parts is A.
+  bool adjoint_data = false;
+  std::vector<double> Ke;        // [ne][B][B]
+  std::vector<double> Y;         // [nnzb][4][B][B]
 };
+
+// Element and interpolation weights of each point (Newton on the element map).
+int mesh_locate(const Mesh& m, int64_t n, const double* pts, int64_t* elem, double* weights,
+                std::string& err);
 
 // Returns 0 or an agg_status; err gets a message.
 int mesh_build(Mesh& m, std::string& err);

@@ -256,6 +256,7 @@ int mesh_build(Mesh& m, std::string& err) {
 
   m.Me.assign((size_t)ne * B * B, 0.0);
   std::vector<double> Ke((size_t)ne * B * B, 0.0);
+  const bool adj = m.adjoint_data;
   m.vol.assign(ne, 0.0);
   int bad_jac = 0;
 
@@ -349,6 +350,7 @@ int mesh_build(Mesh& m, std::string& err) {
   const int64_t nnzb = m.A.rowptr[ne];
   m.A.col.assign(nnzb, 0);
   m.A.val.assign((size_t)nnzb * B * B, 0.0);
+  if (adj) m.Y.assign((size_t)nnzb * 4 * B * B, 0.0);
   int bad_face = 0;
 
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : bad_face)
@@ -467,6 +469,36 @@ int mesh_build(Mesh& m, std::string& err) {
         sig[iq] = alpha * s;
       }
       double* Aoff = &m.A.val[(size_t)(base + slot_of[i]) * B * B];
+      if (adj) {
+        // part of this face's terms built with D_e (e on the + side): its
+        // consistency terms and half of the penalty
+        std::vector<double> sp(Qf);
+        for (int iq = 0; iq < Qf; ++iq) {
+          double s2 = 0.0;
+          for (int k = 0; k < dim; ++k)
+            for (int l = 0; l < dim; ++l) s2 += nrm[iq][k] * Dp[k * dim + l] * nrm[iq][l];
+          sp[iq] = 0.5 * alpha * s2;
+        }
+        double* Y = &m.Y[(size_t)(base + slot_of[i]) * 4 * B * B];
+        for (int a = 0; a < B; ++a)
+          for (int b = 0; b < B; ++b) {
+            double yee = 0.0, yen = 0.0, yne = 0.0, ynn = 0.0;
+            for (int iq = 0; iq < Qf; ++iq) {
+              const double w = wdS[iq], s2 = sp[iq];
+              const double pa = PHP[iq * B + a], pb = PHP[iq * B + b];
+              const double ma = PHM[iq * B + a], mb = PHM[iq * B + b];
+              const double fa = FLP[iq * B + a], fb = FLP[iq * B + b];
+              yee += w * (-0.5 * pa * fb - 0.5 * pb * fa + s2 * pa * pb);
+              yen += w * (0.5 * mb * fa - s2 * pa * mb);
+              yne += w * (0.5 * ma * fb - s2 * ma * pb);
+              ynn += w * (s2 * ma * mb);
+            }
+            Y[0 * B * B + a * B + b] = yee;
+            Y[1 * B * B + a * B + b] = yen;
+            Y[2 * B * B + a * B + b] = yne;
+            Y[3 * B * B + a * B + b] = ynn;
+          }
+      }
       for (int a = 0; a < B; ++a)
         for (int b = 0; b < B; ++b) {
           double spp = 0.0, spm = 0.0;
@@ -483,6 +515,62 @@ int mesh_build(Mesh& m, std::string& err) {
     }
   }
   if (bad_face) { err = "non-conforming face (quadrature points do not coincide)"; return AGG_EINVAL; }
+  if (adj) m.Ke.swap(Ke);
+  return AGG_OK;
+}
+
+int mesh_locate(const Mesh& m, int64_t n, const double* pts, int64_t* elem, double* weights, std::string& err) {
+  const int dim = m.dim, V = 1 << dim, n1 = m.p + 1, B = m.B;
+  Tables1D t = make_tables(m.p, m.p + 2);
+  std::vector<double> lo((size_t)m.ne * dim, 1e300), hi((size_t)m.ne * dim, -1e300);
+  for (int64_t e = 0; e < m.ne; ++e)
+    for (int c = 0; c < V; ++c)
+      for (int k = 0; k < dim; ++k) {
+        const double x = m.X[m.cells[e * V + c] * dim + k];
+        lo[e * dim + k] = std::min(lo[e * dim + k], x);
+        hi[e * dim + k] = std::max(hi[e * dim + k], x);
+      }
+  int missing = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : missing)
+  for (int64_t s = 0; s < n; ++s) {
+    const double* x = pts + s * dim;
+    bool found = false;
+    for (int64_t e = 0; e < m.ne && !found; ++e) {
+      bool inside = true;
+      for (int k = 0; k < dim; ++k)
+        inside = inside && x[k] >= lo[e * dim + k] - 1e-12 && x[k] <= hi[e * dim + k] + 1e-12;
+      if (!inside) continue;
+      double Xc[8 * MAXD];
+      for (int c = 0; c < V; ++c)
+        for (int k = 0; k < dim; ++k) Xc[c * dim + k] = m.X[m.cells[e * V + c] * dim + k];
+      double xi[MAXD] = {0.5, 0.5, 0.5};
+      for (int it = 0; it < 50; ++it) {
+        double xx[MAXD], J[MAXD][MAXD], Ji[MAXD][MAXD];
+        map_point(dim, Xc, xi, xx, J);
+        det_inv(dim, J, Ji);
+        double mx = 0.0;
+        for (int k = 0; k < dim; ++k) {
+          double d = 0.0;
+          for (int l = 0; l < dim; ++l) d += Ji[k][l] * (xx[l] - x[l]);
+          xi[k] -= d;
+          mx = std::max(mx, std::fabs(d));
+        }
+        if (mx < 1e-15) break;
+      }
+      bool in_ref = true;
+      for (int k = 0; k < dim; ++k) in_ref = in_ref && xi[k] >= -1e-10 && xi[k] <= 1.0 + 1e-10;
+      if (!in_ref) continue;
+      for (int k = 0; k < dim; ++k) xi[k] = std::min(1.0, std::max(0.0, xi[k]));
+      Basis b;
+      tensor_basis(t, dim, xi, b);
+      elem[s] = e;
+      for (int i = 0; i < B; ++i) weights[s * B + i] = b.phi[i];
+      found = true;
+    }
+    if (!found) missing += 1;
+  }
+  (void)n1;
+  if (missing) { err = std::to_string(missing) + " point(s) outside the mesh"; return AGG_EINVAL; }
   return AGG_OK;
 }
 

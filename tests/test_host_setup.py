@@ -123,3 +123,46 @@ def test_paper_penalty_reported_not_spd():
     with pytest.raises(aggmg.AggError) as e:
         aggmg.HostHierarchy(mesh, 20.0, wl.maps)
     assert e.value.status == aggmg.AGG_ENOTSPD
+
+
+@pytest.mark.parametrize("dim,p,jit", [(2, 2, 0.2), (3, 1, 0.15)])
+def test_adjoint_forms_match_oracle_attribution(dim, p, jit):
+    mesh_ = W.box_mesh(dim, 3, jitter=jit, seed=10)
+    if dim == 2:
+        D = W.conductivity_from_fibres(W.planar_fibres(mesh_.n_elements, 30.0), 1.2e-3, 2.5e-4)
+    else:
+        D = W.conductivity_from_fibres(W.rotating_fibres_z(mesh_.centroids()), 1.2e-3, 2.5e-4)
+    Ke_o, ep, em, Yp, Ym = osipg.attributed_forms(mesh_.vertices, mesh_.elements, D, p, 1, 10.0)
+    m = aggmg.Mesh(mesh_.vertices, mesh_.elements, D, p, adjoint_data=True)
+    Ke, Y = m.adjoint_forms()
+    rp, cols, _ = m.stiffness_bsr()
+    scale = np.abs(Yp).max()
+    np.testing.assert_allclose(Ke, Ke_o, atol=1e-14 * np.abs(Ke_o).max())
+    face_of = {(int(a), int(b)): f for f, (a, b) in enumerate(zip(ep, em))}
+    for e in range(mesh_.n_elements):
+        for k in range(rp[e], rp[e + 1]):
+            n = int(cols[k])
+            if n == e:
+                assert np.all(Y[k] == 0.0)
+                continue
+            if e < n:
+                f = face_of[(e, n)]
+                exp = [Yp[f, 0, 0], Yp[f, 0, 1], Yp[f, 1, 0], Yp[f, 1, 1]]
+            else:
+                f = face_of[(n, e)]
+                exp = [Ym[f, 1, 1], Ym[f, 1, 0], Ym[f, 0, 1], Ym[f, 0, 0]]
+            for b in range(4):
+                np.testing.assert_allclose(Y[k, b], exp[b], atol=1e-13 * scale)
+
+
+def test_locate_matches_oracle():
+    mesh_ = W.box_mesh(2, 6, jitter=0.2, seed=11)
+    D = W.isotropic_conductivity(mesh_.n_elements, 2, 1e-3)
+    pts = np.random.default_rng(12).uniform(0, 1, size=(50, 2))
+    eo, wo = osipg.locate_points(mesh_.vertices, mesh_.elements, 2, pts)
+    m = aggmg.Mesh(mesh_.vertices, mesh_.elements, D, 2)
+    el, w = m.locate(pts)
+    assert np.array_equal(el, eo)
+    np.testing.assert_allclose(w, wo, atol=1e-12)
+    with pytest.raises(aggmg.AggError):
+        m.locate(np.array([[1.5, 0.5]]))
