@@ -51,6 +51,7 @@ WORKLOADS = {
     "jsquare2d": ("W.jittered_square_2d(n={n}, degree=2, n_levels=4)", 512),
     "jcube3d": ("W.jittered_cube_3d(n={n}, degree=2, n_levels=4, group=4)", 64),
     "shell": ("W.ventricle_shell()", None),
+    "cube3d_q3": ("W.cube_3d_adjoint(n={n})", 48),
     "square2d": ("W.square_2d_fhn({n}, 1)", 16),
 }
 

@@ -11,8 +11,11 @@ import time
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-OUT = os.path.join(HERE, "_build")
+# AGG_BUILD_DIR / AGG_NVCC_FLAGS select another build folder and extra nvcc
+# flags (used to compare tuning variants side by side)
+OUT = os.environ.get("AGG_BUILD_DIR", os.path.join(HERE, "_build"))
 LIB = os.path.join(OUT, "libaggmg.so")
+EXTRA = os.environ.get("AGG_NVCC_FLAGS", "").split()
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -43,7 +46,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     objs = []
     for f in cu:
         o = os.path.join(OUT, f + ".o")
-        cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp",
+        cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", *EXTRA, "-Xcompiler", "-fPIC,-fopenmp",
                "-c", os.path.join(CSRC, f), "-o", o]
         jobs.append((f, cmd))
         objs.append(o)

@@ -20,6 +20,18 @@ EngineBase* make_engine_b8(int);
 EngineBase* make_engine_b9(int);
 EngineBase* make_engine_b16(int);
 EngineBase* make_engine_b27(int);
+EngineBase* make_engine_b64_f64();
+EngineBase* make_engine_b64_f32();
+EngineBase* make_engine_b64_bf16();
+
+static EngineBase* make_engine_b64(int precision) {
+  switch (precision) {
+    case AGG_F64: return make_engine_b64_f64();
+    case AGG_F32: return make_engine_b64_f32();
+    case AGG_F32_BF16SMOOTH: return make_engine_b64_bf16();
+    default: return nullptr;
+  }
+}
 
 EngineBase* make_engine(int B, int precision) {
   switch (B) {
@@ -28,6 +40,7 @@ EngineBase* make_engine(int B, int precision) {
     case 9: return make_engine_b9(precision);
     case 16: return make_engine_b16(precision);
     case 27: return make_engine_b27(precision);
+    case 64: return make_engine_b64(precision);
     default: return nullptr;
   }
 }

@@ -220,31 +220,44 @@ static __global__ void k_ionic_update(IonicParams prm, double dt, int64_t n, con
 //   w <- w + dt H(u, w);  f = I_app(t_{n+1}) mask - chi I(u, w_new);
 //   b_e = M_e (c u_e + f_e)   (ionic current interpolation)
 template <int B>
-static __global__ void __launch_bounds__(NT) k_ionic_rhs(const double* __restrict__ Me, const double* __restrict__ u,
-                                                  double* __restrict__ w, const double* __restrict__ mask,
-                                                  double* __restrict__ b, IonicParams prm, double dt, double chi,
-                                                  double c, double iapp_value, int64_t iapp_steps,
-                                                  const int64_t* __restrict__ step, int64_t nslices) {
+static __global__ void __launch_bounds__(UnitThreads<B>::value)
+    k_ionic_rhs(const double* __restrict__ Me, const double* __restrict__ u, double* __restrict__ w,
+                const double* __restrict__ mask, double* __restrict__ b, IonicParams prm, double dt, double chi,
+                double c, double iapp_value, int64_t iapp_steps, const int64_t* __restrict__ step, int64_t nslices) {
+  constexpr int NTB = UnitThreads<B>::value;
   constexpr int KP = Pad<double, B>::KP;
-  const int64_t unit = (int64_t)blockIdx.x * NT + threadIdx.x;
+  const int64_t unit = (int64_t)blockIdx.x * NTB + threadIdx.x;
   const int64_t slice = unit / SL;
   const int lane = threadIdx.x & 31;
   if (slice >= nslices) return;
   const size_t o = (size_t)unit * B;
   const double ia = (*step < iapp_steps) ? iapp_value : 0.0;
-  double t[B], acc[B];
-#pragma unroll
-  for (int r = 0; r < B; ++r) {
+  // per DoF: ionic update and the nodal load c u + I_app mask - chi I(u, w_new)
+  auto nodal = [&](int r) {
     const double ur = u[o + r];
     double I, H;
     ionic_eval(prm, ur, w[o + r], I, H);
     const double wn = w[o + r] + dt * H;
     w[o + r] = wn;
     ionic_eval(prm, ur, wn, I, H);
-    t[r] = c * ur + ia * mask[o + r] - chi * I;
-    acc[r] = 0.0;
+    return c * ur + ia * mask[o + r] - chi * I;
+  };
+  double acc[B];
+#pragma unroll
+  for (int r = 0; r < B; ++r) acc[r] = 0.0;
+  const double* Mb = Me + (size_t)slice * SL * KP;
+  if constexpr (B > 32) {
+    __shared__ double tsh[B * NTB];
+    double* ts = tsh + threadIdx.x;
+#pragma unroll
+    for (int r = 0; r < B; ++r) ts[r * NTB] = nodal(r);
+    block_mv<double, double, B, NTB>(Mb, lane, ts, acc);
+  } else {
+    double t[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) t[r] = nodal(r);
+    block_mv<double, double, B>(Mb, lane, t, acc);
   }
-  block_mv<double, double, B>(Me + (size_t)slice * SL * KP, lane, t, acc);
 #pragma unroll
   for (int r = 0; r < B; ++r) b[o + r] = acc[r];
 }
@@ -277,21 +290,28 @@ __device__ __forceinline__ void ionic_jac(const IonicParams& p, double u, double
 //   ubar_n = q (c - chi I_u(u_n, w_np1)) + dt H_u(u_n, w_n) w~,
 //   wbar_n = w~ (1 + dt H_w(u_n, w_n)),   with w_np1 = w_n + dt H(u_n, w_n).
 template <int B>
-static __global__ void __launch_bounds__(NT) k_adj_pointwise(const double* __restrict__ Me, const double* __restrict__ lam,
-                                                             const double* __restrict__ u_n, const double* __restrict__ w_n,
-                                                             double* __restrict__ ubar, double* __restrict__ wbar,
-                                                             IonicParams prm, double dt, double chi, double c,
-                                                             int64_t nslices) {
+static __global__ void __launch_bounds__(UnitThreads<B>::value)
+    k_adj_pointwise(const double* __restrict__ Me, const double* __restrict__ lam, const double* __restrict__ u_n,
+                    const double* __restrict__ w_n, double* __restrict__ ubar, double* __restrict__ wbar,
+                    IonicParams prm, double dt, double chi, double c, int64_t nslices) {
+  constexpr int NTB = UnitThreads<B>::value;
   constexpr int KP = Pad<double, B>::KP;
-  const int64_t unit = (int64_t)blockIdx.x * NT + threadIdx.x;
+  const int64_t unit = (int64_t)blockIdx.x * NTB + threadIdx.x;
   const int64_t slice = unit / SL;
   const int lane = threadIdx.x & 31;
   if (slice >= nslices) return;
   const size_t o = (size_t)unit * B;
-  double lv[B], q[B];
+  double q[B];
 #pragma unroll
-  for (int r = 0; r < B; ++r) { lv[r] = lam[o + r]; q[r] = 0.0; }
-  block_mv<double, double, B>(Me + (size_t)slice * SL * KP, lane, lv, q);
+  for (int r = 0; r < B; ++r) q[r] = 0.0;
+  if constexpr (B > 32) {
+    block_mv<double, double, B>(Me + (size_t)slice * SL * KP, lane, lam + o, q);
+  } else {
+    double lv[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) lv[r] = lam[o + r];
+    block_mv<double, double, B>(Me + (size_t)slice * SL * KP, lane, lv, q);
+  }
 #pragma unroll
   for (int r = 0; r < B; ++r) {
     const double un = u_n[o + r], wn = w_n[o + r];
@@ -311,42 +331,38 @@ static __global__ void __launch_bounds__(NT) k_adj_pointwise(const double* __res
 // with Ke the volume form and Y_e,F the face terms built with D_e (four
 // sliced blocks per stiffness slot, in the slot order of the fine operator).
 template <int B>
-static __global__ void __launch_bounds__(NT) k_grad_logD(SellView<double> A, const double* __restrict__ Ke,
-                                                         const double* __restrict__ Y, const double* __restrict__ lam,
-                                                         const double* __restrict__ u, const int64_t* __restrict__ perm,
-                                                         double* __restrict__ grad, int64_t n) {
+static __global__ void __launch_bounds__(UnitThreads<B>::value)
+    k_grad_logD(SellView<double> A, const double* __restrict__ Ke, const double* __restrict__ Y,
+                const double* __restrict__ lam, const double* __restrict__ u, const int64_t* __restrict__ perm,
+                double* __restrict__ grad, int64_t n) {
+  constexpr int NTB = UnitThreads<B>::value;
   constexpr int KP = Pad<double, B>::KP;
-  const int64_t unit = (int64_t)blockIdx.x * NT + threadIdx.x;
+  const int64_t unit = (int64_t)blockIdx.x * NTB + threadIdx.x;
   const int64_t slice = unit / SL;
   const int lane = threadIdx.x & 31;
   if (slice >= A.nslices) return;
   const size_t o = (size_t)unit * B;
-  double le[B], ue[B], t[B];
+  // sum_r l[r] (M1 x1 + M2 x2)[r] for two sliced blocks (M2 may be null)
+  auto bilin = [&](const double* l, const double* M1, const double* x1, const double* M2, const double* x2) {
+    double t[B];
 #pragma unroll
-  for (int r = 0; r < B; ++r) { le[r] = lam[o + r]; ue[r] = u[o + r]; t[r] = 0.0; }
-  block_mv<double, double, B>(Ke + (size_t)slice * SL * KP, lane, ue, t);
-  double g = 0.0;
+    for (int r = 0; r < B; ++r) t[r] = 0.0;
+    block_mv<double, double, B>(M1, lane, x1, t);
+    if (M2) block_mv<double, double, B>(M2, lane, x2, t);
+    double s = 0.0;
 #pragma unroll
-  for (int r = 0; r < B; ++r) g += le[r] * t[r];
+    for (int r = 0; r < B; ++r) s += l[r] * t[r];
+    return s;
+  };
+  double g = bilin(lam + o, Ke + (size_t)slice * SL * KP, u + o, nullptr, nullptr);
   const int s0 = A.slice_ptr[slice], s1 = A.slice_ptr[slice + 1];
   for (int j = s0; j < s1; ++j) {
     const int col = A.cols[(size_t)j * SL + lane];
     if (col == unit) continue;                 // diagonal or padding slot
-    double ln[B], un[B], t1[B], t2[B];
-#pragma unroll
-    for (int r = 0; r < B; ++r) {
-      ln[r] = lam[(size_t)col * B + r];
-      un[r] = u[(size_t)col * B + r];
-      t1[r] = 0.0;
-      t2[r] = 0.0;
-    }
     const double* Yj = Y + (size_t)j * 4 * SL * KP;
-    block_mv<double, double, B>(Yj, lane, ue, t1);
-    block_mv<double, double, B>(Yj + (size_t)SL * KP, lane, un, t1);
-    block_mv<double, double, B>(Yj + (size_t)2 * SL * KP, lane, ue, t2);
-    block_mv<double, double, B>(Yj + (size_t)3 * SL * KP, lane, un, t2);
-#pragma unroll
-    for (int r = 0; r < B; ++r) g += le[r] * t1[r] + ln[r] * t2[r];
+    const double* un = u + (size_t)col * B;
+    g += bilin(lam + o, Yj, u + o, Yj + (size_t)SL * KP, un);
+    g += bilin(lam + (size_t)col * B, Yj + (size_t)2 * SL * KP, u + o, Yj + (size_t)3 * SL * KP, un);
   }
   if (unit < n) grad[perm[unit]] -= g;
 }

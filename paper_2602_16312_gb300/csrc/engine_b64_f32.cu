@@ -1,0 +1,7 @@
+// Engine instantiation for element blocks of B = 64 DoFs (3D Q3), one
+// precision per translation unit to keep the parallel build short.
+#include "engine_impl.cuh"
+
+namespace aggmg {
+EngineBase* make_engine_b64_f32() { return new Engine<float, float, 64>(); }
+}  // namespace aggmg

@@ -22,7 +22,7 @@
 namespace aggmg {
 
 constexpr int SL = 32;          // units per slice
-constexpr int NT = 128;         // threads per block for unit kernels
+constexpr int NT = 128;         // threads per block of the unit kernels (B <= 32)
 constexpr int RED_BLOCKS = 1216; // fixed grid of the reduction kernels (152 SMs x 8)
 constexpr int RED_NT = 256;
 
@@ -86,11 +86,36 @@ template <> struct ChunkLoad<__nv_bfloat16, float> {
   }
 };
 
-// acc[r] += sum_c M[r][c] x[c] for one sliced block M (storage TS, math A)
-template <typename TS, typename A, int B>
+// Threads per block of the unit kernels: 128, or 64 for 64-DoF blocks whose
+// per-thread vectors are staged in shared memory.
+template <int B> struct UnitThreads {
+  static constexpr int value = (B > 32) ? 64 : 128;
+};
+
+// acc[r] += sum_c M[r][c] x[c*XS] for one sliced block M (storage TS, math
+// A). x may be a register array (XS = 1, fully unrolled indices), a global
+// pointer (neighbour blocks, read through L1) or a strided shared-memory slot.
+template <typename TS, typename A, int B, int XS = 1>
 __device__ __forceinline__ void block_mv(const TS* base, int lane, const A* x, A* acc) {
   constexpr int VW = ChunkLoad<TS, A>::VW;
   constexpr int NCH = (B * B + VW - 1) / VW;
+  if constexpr (B > 32) {
+    // large blocks: loop over the columns (chunks never straddle a column
+    // since VW divides B), rows unrolled, so acc keeps static indices
+    static_assert(B % VW == 0, "column-aligned chunks");
+#pragma unroll 1
+    for (int c = 0; c < B; ++c) {
+      const A xc = x[c * XS];
+#pragma unroll
+      for (int rr = 0; rr < B / VW; ++rr) {
+        A v[VW];
+        ChunkLoad<TS, A>::load(base, c * (B / VW) + rr, lane, v);
+#pragma unroll
+        for (int t = 0; t < VW; ++t) acc[rr * VW + t] += v[t] * xc;
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int ch = 0; ch < NCH; ++ch) {
     A v[VW];
@@ -98,12 +123,12 @@ __device__ __forceinline__ void block_mv(const TS* base, int lane, const A* x, A
 #pragma unroll
     for (int t = 0; t < VW; ++t) {
       const int k = ch * VW + t;
-      if (k < B * B) acc[k % B] += v[t] * x[k / B];
+      if (k < B * B) acc[k % B] += v[t] * x[(k / B) * XS];
     }
   }
 }
-// acc[c] += sum_r M[r][c] x[r] (transposed block)
-template <typename TS, typename A, int B>
+// acc[c] += sum_r M[r][c] x[r*XS] (transposed block)
+template <typename TS, typename A, int B, int XS = 1>
 __device__ __forceinline__ void block_mtv(const TS* base, int lane, const A* x, A* acc) {
   constexpr int VW = ChunkLoad<TS, A>::VW;
   constexpr int NCH = (B * B + VW - 1) / VW;
@@ -114,8 +139,28 @@ __device__ __forceinline__ void block_mtv(const TS* base, int lane, const A* x, 
 #pragma unroll
     for (int t = 0; t < VW; ++t) {
       const int k = ch * VW + t;
-      if (k < B * B) acc[k / B] += v[t] * x[k % B];
+      if (k < B * B) acc[k / B] += v[t] * x[(k % B) * XS];
     }
+  }
+}
+
+// out[c] = sum_r M[r][c] x[r] for large blocks (B > 32): x in registers,
+// one output at a time through a pointer
+template <typename TS, typename A, int B>
+__device__ __forceinline__ void block_mtv_out(const TS* base, int lane, const A* x, A* out) {
+  constexpr int VW = ChunkLoad<TS, A>::VW;
+  static_assert(B % VW == 0, "column-aligned chunks");
+#pragma unroll 1
+  for (int c = 0; c < B; ++c) {
+    A s = A(0);
+#pragma unroll
+    for (int rr = 0; rr < B / VW; ++rr) {
+      A v[VW];
+      ChunkLoad<TS, A>::load(base, c * (B / VW) + rr, lane, v);
+#pragma unroll
+      for (int t = 0; t < VW; ++t) s += v[t] * x[rr * VW + t];
+    }
+    out[c] = s;
   }
 }
 
@@ -127,19 +172,46 @@ struct SellView {
   int64_t nslices;
 };
 
+// Slots whose neighbour blocks are fetched together before their matrix
+// blocks stream in: for small float32 blocks the column-id -> x-gather chain
+// would otherwise serialise two memory latencies per slot.
+#ifndef AGG_SLOT_PREFETCH
+#define AGG_SLOT_PREFETCH 1
+#endif
+template <typename T, int B> struct SlotPrefetch {
+  static constexpr int value =
+      (sizeof(T) == 4 && B <= 9) ? AGG_SLOT_PREFETCH : ((sizeof(T) == 4 && B <= 16) ? 4 : 1);
+};
+
 // y_u = sum_slots A_{u,col} x_col for the thread's unit (acc zeroed by caller)
 template <typename T, int B>
 __device__ __forceinline__ void sell_row(const SellView<T>& A, int64_t slice, int lane, const T* __restrict__ x,
                                          T* acc) {
   constexpr int KP = Pad<T, B>::KP;
+  constexpr int PF = SlotPrefetch<T, B>::value;
   const int s0 = A.slice_ptr[slice], s1 = A.slice_ptr[slice + 1];
-  for (int j = s0; j < s1; ++j) {
-    const int col = A.cols[(size_t)j * SL + lane];
-    const T* xb = x + (size_t)col * B;
-    T xv[B];
+  if constexpr (B > 32) {
+    for (int j = s0; j < s1; ++j) {
+      const int col = A.cols[(size_t)j * SL + lane];
+      block_mv<T, T, B>(A.vals + (size_t)j * SL * KP, lane, x + (size_t)col * B, acc);
+    }
+    return;
+  }
+  for (int j0 = s0; j0 < s1; j0 += PF) {
+    const int ns = min(PF, s1 - j0);     // uniform across the warp (one slice per warp)
+    int col[PF];
 #pragma unroll
-    for (int c = 0; c < B; ++c) xv[c] = xb[c];
-    block_mv<T, T, B>(A.vals + (size_t)j * SL * KP, lane, xv, acc);
+    for (int t = 0; t < PF; ++t) col[t] = (t < ns) ? A.cols[(size_t)(j0 + t) * SL + lane] : 0;
+    T xv[PF][B];
+#pragma unroll
+    for (int t = 0; t < PF; ++t) {
+      const T* xb = x + (size_t)col[t] * B;
+#pragma unroll
+      for (int c = 0; c < B; ++c) xv[t][c] = (t < ns) ? xb[c] : T(0);
+    }
+#pragma unroll
+    for (int t = 0; t < PF; ++t)
+      if (t < ns) block_mv<T, T, B>(A.vals + (size_t)(j0 + t) * SL * KP, lane, xv[t], acc);
   }
 }
 
@@ -194,10 +266,12 @@ __device__ __forceinline__ double sum_partials(const double* partials, int n) {
 // ---------------------------------------------------------------- SpMV
 // MODE 0: y = A x;  MODE 1: y = rhs - A x;  MODE 2: y = A x and (x, y) -> alpha
 template <typename T, int B, int MODE>
-static __global__ void __launch_bounds__(NT) k_spmv(SellView<T> A, const T* __restrict__ x, const T* __restrict__ rhs,
-                                             T* __restrict__ y, double* partials, CGState* st) {
+static __global__ void __launch_bounds__(UnitThreads<B>::value)
+    k_spmv(SellView<T> A, const T* __restrict__ x, const T* __restrict__ rhs, T* __restrict__ y, double* partials,
+           CGState* st) {
+  constexpr int NTB = UnitThreads<B>::value;
   if (st && st->done) return;
-  const int64_t unit = (int64_t)blockIdx.x * NT + threadIdx.x;
+  const int64_t unit = (int64_t)blockIdx.x * NTB + threadIdx.x;
   const int64_t slice = unit / SL;
   const int lane = threadIdx.x & 31;
   double part = 0.0;
@@ -218,8 +292,8 @@ static __global__ void __launch_bounds__(NT) k_spmv(SellView<T> A, const T* __re
     }
   }
   if (MODE == 2) {
-    if (partial_and_last<NT>(part, partials, &st->ticket[0])) {
-      double pq = sum_partials<NT>(partials, gridDim.x);
+    if (partial_and_last<NTB>(part, partials, &st->ticket[0])) {
+      double pq = sum_partials<NTB>(partials, gridDim.x);
       if (threadIdx.x == 0) {
         st->pq = pq;
         st->alpha = st->rho / pq;
@@ -233,33 +307,55 @@ static __global__ void __launch_bounds__(NT) k_spmv(SellView<T> A, const T* __re
 // KIND 0: d = c2 Dinv rhs, x_new = d                          (start from x = 0)
 // KIND 1: d = c2 Dinv (rhs - A x_old), x_new = x_old + d      (first step, x given)
 // KIND 2: d = c1 d + c2 Dinv (rhs - A x_old), x_new = x_old + d
+// Blocks of more than 32 DoFs keep the residual in the thread's own strided
+// shared-memory slot (read by that thread only) instead of registers.
 template <typename T, typename TD, int B, int KIND>
-static __global__ void __launch_bounds__(NT) k_cheb(SellView<T> A, const TD* __restrict__ Dinv, const T* __restrict__ rhs,
-                                             const T* __restrict__ x_old, T* __restrict__ x_new, T* __restrict__ d,
-                                             T c1, T c2, int64_t nslices, const CGState* st) {
+static __global__ void __launch_bounds__(UnitThreads<B>::value)
+    k_cheb(SellView<T> A, const TD* __restrict__ Dinv, const T* __restrict__ rhs, const T* __restrict__ x_old,
+           T* __restrict__ x_new, T* __restrict__ d, T c1, T c2, int64_t nslices, const CGState* st) {
+  constexpr int NTB = UnitThreads<B>::value;
   if (st && st->done) return;
   constexpr int KPD = Pad<TD, B>::KP;
-  const int64_t unit = (int64_t)blockIdx.x * NT + threadIdx.x;
+  const int64_t unit = (int64_t)blockIdx.x * NTB + threadIdx.x;
   const int64_t slice = unit / SL;
   const int lane = threadIdx.x & 31;
   if (slice >= nslices) return;
   const size_t o = (size_t)unit * B;
-  T t[B];
-  if (KIND == 0) {
-#pragma unroll
-    for (int r = 0; r < B; ++r) t[r] = rhs[o + r];
-  } else {
-    T acc[B];
-#pragma unroll
-    for (int r = 0; r < B; ++r) acc[r] = T(0);
-    sell_row<T, B>(A, slice, lane, x_old, acc);
-#pragma unroll
-    for (int r = 0; r < B; ++r) t[r] = rhs[o + r] - acc[r];
-  }
+  const TD* Db = Dinv + (size_t)slice * SL * KPD;
   T s[B];
 #pragma unroll
   for (int r = 0; r < B; ++r) s[r] = T(0);
-  block_mv<TD, T, B>(Dinv + (size_t)slice * SL * KPD, lane, t, s);
+  if constexpr (B > 32) {
+    __shared__ T tsh[B * NTB];
+    T* ts = tsh + threadIdx.x;
+    if (KIND == 0) {
+      block_mv<TD, T, B>(Db, lane, rhs + o, s);
+    } else {
+      {
+        T acc[B];
+#pragma unroll
+        for (int r = 0; r < B; ++r) acc[r] = T(0);
+        sell_row<T, B>(A, slice, lane, x_old, acc);
+#pragma unroll
+        for (int r = 0; r < B; ++r) ts[r * NTB] = rhs[o + r] - acc[r];
+      }
+      block_mv<TD, T, B, NTB>(Db, lane, ts, s);
+    }
+  } else {
+    T t[B];
+    if (KIND == 0) {
+#pragma unroll
+      for (int r = 0; r < B; ++r) t[r] = rhs[o + r];
+    } else {
+      T acc[B];
+#pragma unroll
+      for (int r = 0; r < B; ++r) acc[r] = T(0);
+      sell_row<T, B>(A, slice, lane, x_old, acc);
+#pragma unroll
+      for (int r = 0; r < B; ++r) t[r] = rhs[o + r] - acc[r];
+    }
+    block_mv<TD, T, B>(Db, lane, t, s);
+  }
 #pragma unroll
   for (int r = 0; r < B; ++r) {
     T dn = (KIND == 2) ? c1 * d[o + r] + c2 * s[r] : c2 * s[r];
@@ -271,23 +367,40 @@ static __global__ void __launch_bounds__(NT) k_cheb(SellView<T> A, const TD* __r
 // ---------------------------------------------------------------- transfers
 // S_u = P_u^T (rhs_u - (A x)_u): residual of the pre-smoothed iterate, restricted
 template <typename T, int B>
-static __global__ void __launch_bounds__(NT) k_resid_restrict(SellView<T> A, const T* __restrict__ P, const T* __restrict__ rhs,
-                                                       const T* __restrict__ x, T* __restrict__ S, const CGState* st) {
+static __global__ void __launch_bounds__(UnitThreads<B>::value)
+    k_resid_restrict(SellView<T> A, const T* __restrict__ P, const T* __restrict__ rhs, const T* __restrict__ x,
+                     T* __restrict__ S, const CGState* st) {
+  constexpr int NTB = UnitThreads<B>::value;
   if (st && st->done) return;
   constexpr int KP = Pad<T, B>::KP;
-  const int64_t unit = (int64_t)blockIdx.x * NT + threadIdx.x;
+  const int64_t unit = (int64_t)blockIdx.x * NTB + threadIdx.x;
   const int64_t slice = unit / SL;
   const int lane = threadIdx.x & 31;
   if (slice >= A.nslices) return;
   const size_t o = (size_t)unit * B;
-  T acc[B];
+  const T* Pb = P + (size_t)slice * SL * KP;
+  T s[B];
 #pragma unroll
-  for (int r = 0; r < B; ++r) acc[r] = T(0);
-  sell_row<T, B>(A, slice, lane, x, acc);
-  T t[B], s[B];
+  for (int r = 0; r < B; ++r) s[r] = T(0);
+  if constexpr (B > 32) {
+    T acc[B];
 #pragma unroll
-  for (int r = 0; r < B; ++r) { t[r] = rhs[o + r] - acc[r]; s[r] = T(0); }
-  block_mtv<T, T, B>(P + (size_t)slice * SL * KP, lane, t, s);
+    for (int r = 0; r < B; ++r) acc[r] = T(0);
+    sell_row<T, B>(A, slice, lane, x, acc);
+#pragma unroll
+    for (int r = 0; r < B; ++r) acc[r] = rhs[o + r] - acc[r];
+    block_mtv_out<T, T, B>(Pb, lane, acc, S + o);
+    return;
+  } else {
+    T acc[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) acc[r] = T(0);
+    sell_row<T, B>(A, slice, lane, x, acc);
+    T t[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) t[r] = rhs[o + r] - acc[r];
+    block_mtv<T, T, B>(Pb, lane, t, s);
+  }
 #pragma unroll
   for (int j = 0; j < B; ++j) S[o + j] = s[j];
 }
@@ -308,21 +421,29 @@ static __global__ void k_segsum(const int64_t* __restrict__ child_ptr, const T* 
 
 // x_u += P_u e_{parent(u)}
 template <typename T, int B>
-static __global__ void __launch_bounds__(NT) k_prolong(const T* __restrict__ P, const int32_t* __restrict__ parent,
-                                                const T* __restrict__ ec, T* __restrict__ x, int64_t nslices,
-                                                const CGState* st) {
+static __global__ void __launch_bounds__(UnitThreads<B>::value)
+    k_prolong(const T* __restrict__ P, const int32_t* __restrict__ parent, const T* __restrict__ ec,
+              T* __restrict__ x, int64_t nslices, const CGState* st) {
+  constexpr int NTB = UnitThreads<B>::value;
   if (st && st->done) return;
   constexpr int KP = Pad<T, B>::KP;
-  const int64_t unit = (int64_t)blockIdx.x * NT + threadIdx.x;
+  const int64_t unit = (int64_t)blockIdx.x * NTB + threadIdx.x;
   const int64_t slice = unit / SL;
   const int lane = threadIdx.x & 31;
   if (slice >= nslices) return;
   const size_t o = (size_t)unit * B;
   const T* eb = ec + (size_t)parent[unit] * B;
-  T ev[B], acc[B];
+  T acc[B];
 #pragma unroll
-  for (int j = 0; j < B; ++j) { ev[j] = eb[j]; acc[j] = T(0); }
-  block_mv<T, T, B>(P + (size_t)slice * SL * KP, lane, ev, acc);
+  for (int j = 0; j < B; ++j) acc[j] = T(0);
+  if constexpr (B > 32) {
+    block_mv<T, T, B>(P + (size_t)slice * SL * KP, lane, eb, acc);
+  } else {
+    T ev[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) ev[j] = eb[j];
+    block_mv<T, T, B>(P + (size_t)slice * SL * KP, lane, ev, acc);
+  }
 #pragma unroll
   for (int r = 0; r < B; ++r) x[o + r] += acc[r];
 }

@@ -30,6 +30,7 @@ CASES = {
     "jsquare2d_q2_12": lambda: W.jittered_square_2d(n=12, n_levels=2),
     "jcube3d_q1_6": lambda: W.jittered_cube_3d(n=6, degree=1, n_levels=3, group=2),
     "jcube3d_q2_4": lambda: W.jittered_cube_3d(n=4, degree=2, n_levels=2, group=2),
+    "cube3d_q3_4": lambda: W.cube_3d_adjoint(n=4, degree=3, n_levels=2),
 }
 
 

@@ -33,6 +33,7 @@ CASES = {
     "jcube3d_q1_6": lambda: W.jittered_cube_3d(n=6, degree=1, n_levels=3, group=2),
     "jcube3d_q2_6": lambda: W.jittered_cube_3d(n=6, degree=2, n_levels=3, group=2),
     "shell_q2": lambda: W.ventricle_shell(16, 8, 4, n_levels=3),
+    "jcube3d_q3_6": lambda: W.jittered_cube_3d(n=6, degree=3, n_levels=3, group=2),
 }
 
 

@@ -26,6 +26,7 @@ def _built():
 CASES = {
     "jsquare2d_q2_30": lambda: W.jittered_square_2d(n=30, n_levels=3),
     "jcube3d_q2_6": lambda: W.jittered_cube_3d(n=6, degree=2, n_levels=3, group=2),
+    "jcube3d_q3_6": lambda: W.jittered_cube_3d(n=6, degree=3, n_levels=3, group=2),
 }
 
 

@@ -31,6 +31,7 @@ CASES = {
     "jcube3d_q1": lambda: W.jittered_cube_3d(n=4, degree=1, n_levels=2, group=2),
     "jcube3d_q2": lambda: W.jittered_cube_3d(n=4, degree=2, n_levels=3, group=2),
     "shell_q2": lambda: W.ventricle_shell(16, 8, 4, n_levels=3),
+    "cube3d_q3": lambda: W.cube_3d_adjoint(n=4, degree=3, n_levels=2),
 }
 
 
