@@ -226,10 +226,9 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
                 double c, double iapp_value, int64_t iapp_steps, const int64_t* __restrict__ step, int64_t nslices) {
   constexpr int NTB = UnitThreads<B>::value;
   constexpr int KP = Pad<double, B>::KP;
-  const int64_t unit = (int64_t)blockIdx.x * NTB + threadIdx.x;
-  const int64_t slice = unit / SL;
   const int lane = threadIdx.x & 31;
-  if (slice >= nslices) return;
+  for (int64_t slice = first_slice<NTB>(); slice < nslices; slice += slice_stride<NTB>()) {
+  const int64_t unit = slice * SL + lane;
   const size_t o = (size_t)unit * B;
   const double ia = (*step < iapp_steps) ? iapp_value : 0.0;
   // per DoF: ionic update and the nodal load c u + I_app mask - chi I(u, w_new)
@@ -260,6 +259,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
   }
 #pragma unroll
   for (int r = 0; r < B; ++r) b[o + r] = acc[r];
+  }
 }
 
 // Partial derivatives of the ionic model at one DoF (I_u, I_w, H_u, H_w).
@@ -296,10 +296,9 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
                     IonicParams prm, double dt, double chi, double c, int64_t nslices) {
   constexpr int NTB = UnitThreads<B>::value;
   constexpr int KP = Pad<double, B>::KP;
-  const int64_t unit = (int64_t)blockIdx.x * NTB + threadIdx.x;
-  const int64_t slice = unit / SL;
   const int lane = threadIdx.x & 31;
-  if (slice >= nslices) return;
+  for (int64_t slice = first_slice<NTB>(); slice < nslices; slice += slice_stride<NTB>()) {
+  const int64_t unit = slice * SL + lane;
   const size_t o = (size_t)unit * B;
   double q[B];
 #pragma unroll
@@ -324,6 +323,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
     ubar[o + r] = q[r] * (c - chi * Iu1) + dt * Hu * wt;
     wbar[o + r] = wt * (1.0 + dt * Hw);
   }
+  }
 }
 
 // Per-element log-conductivity gradient, accumulated in the caller's order:
@@ -337,10 +337,9 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
                 double* __restrict__ grad, int64_t n) {
   constexpr int NTB = UnitThreads<B>::value;
   constexpr int KP = Pad<double, B>::KP;
-  const int64_t unit = (int64_t)blockIdx.x * NTB + threadIdx.x;
-  const int64_t slice = unit / SL;
   const int lane = threadIdx.x & 31;
-  if (slice >= A.nslices) return;
+  for (int64_t slice = first_slice<NTB>(); slice < A.nslices; slice += slice_stride<NTB>()) {
+  const int64_t unit = slice * SL + lane;
   const size_t o = (size_t)unit * B;
   // sum_r l[r] (M1 x1 + M2 x2)[r] for two sliced blocks (M2 may be null)
   auto bilin = [&](const double* l, const double* M1, const double* x1, const double* M2, const double* x2) {
@@ -365,6 +364,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
     g += bilin(lam + (size_t)col * B, Yj + (size_t)2 * SL * KP, u + o, Yj + (size_t)3 * SL * KP, un);
   }
   if (unit < n) grad[perm[unit]] -= g;
+  }
 }
 
 // end of a time step: record the iteration count, advance the clock

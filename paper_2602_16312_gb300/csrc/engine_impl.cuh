@@ -62,6 +62,20 @@ class Engine : public EngineBase {
 
   std::vector<Lev> lev_;
   std::vector<int64_t> nnzb_;
+  int num_sms_ = 152;
+
+  // Grid of a slice-looping unit kernel: all warps resident at once and the
+  // same number of slices per warp (no partial last wave).
+  template <typename K>
+  int64_t bgrid(K kern, int64_t nsl) const {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NTB, 0) != cudaSuccess || nb < 1) nb = 1;
+    const int64_t wpb = NTB / 32;
+    const int64_t maxw = (int64_t)nb * num_sms_ * wpb;
+    const int64_t per = cdiv(nsl, maxw);
+    const int64_t warps = cdiv(nsl, per);
+    return std::max<int64_t>(1, cdiv(warps, wpb));
+  }
   int nlev_ = 0, degree_ = 3;
   SellView<double> A0_{};
   double* Me_ = nullptr;
@@ -176,24 +190,25 @@ class Engine : public EngineBase {
       k_coarse_upper<T><<<g, 256, 0, s>>>(U_, yc_, v.xa, nc_, st_);
       return v.xa;
     }
-    const int64_t g = cdiv(v.nsl * SL, NTB);
     T* xo = v.xa;
     T* xn = v.xb;
     const SellView<T> A = v.A();
-    k_cheb<T, TD, B, 0><<<g, NTB, 0, s>>>(A, v.Dinv, v.rhs, nullptr, xo, v.d, T(0), v.c2[0], v.nsl, st_);
+    const int64_t g0k = bgrid(k_cheb<T, TD, B, 0>, v.nsl), g1k = bgrid(k_cheb<T, TD, B, 1>, v.nsl);
+    const int64_t g2k = bgrid(k_cheb<T, TD, B, 2>, v.nsl);
+    k_cheb<T, TD, B, 0><<<g0k, NTB, 0, s>>>(A, v.Dinv, v.rhs, nullptr, xo, v.d, T(0), v.c2[0], v.nsl, st_);
     for (int k = 1; k < degree_; ++k) {
-      k_cheb<T, TD, B, 2><<<g, NTB, 0, s>>>(A, v.Dinv, v.rhs, xo, xn, v.d, v.c1[k], v.c2[k], v.nsl, st_);
+      k_cheb<T, TD, B, 2><<<g2k, NTB, 0, s>>>(A, v.Dinv, v.rhs, xo, xn, v.d, v.c1[k], v.c2[k], v.nsl, st_);
       std::swap(xo, xn);
     }
     Lev& c = lev_[l + 1];
-    k_resid_restrict<T, B><<<g, NTB, 0, s>>>(A, v.P, v.rhs, xo, v.S, st_);
+    k_resid_restrict<T, B><<<bgrid(k_resid_restrict<T, B>, v.nsl), NTB, 0, s>>>(A, v.P, v.rhs, xo, v.S, st_);
     k_segsum<T, B><<<cdiv(c.n * B, 256), 256, 0, s>>>(c.child_ptr, v.S, c.rhs, c.n, st_);
     T* ec = vc(l + 1, s);
-    k_prolong<T, B><<<g, NTB, 0, s>>>(v.P, v.parent, ec, xo, v.nsl, st_);
-    k_cheb<T, TD, B, 1><<<g, NTB, 0, s>>>(A, v.Dinv, v.rhs, xo, xn, v.d, T(0), v.c2[0], v.nsl, st_);
+    k_prolong<T, B><<<bgrid(k_prolong<T, B>, v.nsl), NTB, 0, s>>>(v.P, v.parent, ec, xo, v.nsl, st_);
+    k_cheb<T, TD, B, 1><<<g1k, NTB, 0, s>>>(A, v.Dinv, v.rhs, xo, xn, v.d, T(0), v.c2[0], v.nsl, st_);
     std::swap(xo, xn);
     for (int k = 1; k < degree_; ++k) {
-      k_cheb<T, TD, B, 2><<<g, NTB, 0, s>>>(A, v.Dinv, v.rhs, xo, xn, v.d, v.c1[k], v.c2[k], v.nsl, st_);
+      k_cheb<T, TD, B, 2><<<g2k, NTB, 0, s>>>(A, v.Dinv, v.rhs, xo, xn, v.d, v.c1[k], v.c2[k], v.nsl, st_);
       std::swap(xo, xn);
     }
     return xo;
@@ -219,14 +234,14 @@ class Engine : public EngineBase {
 
   void launch_init(cudaStream_t s, unsigned long long cond, int use_cond) {
     k_cg_begin<<<1, 1, 0, s>>>(st_, cond, use_cond);
-    k_spmv<double, B, 1><<<g0(), NTB, 0, s>>>(A0_, x_, b_, r_, nullptr, nullptr);
+    k_spmv<double, B, 1><<<bgrid(k_spmv<double, B, 1>, lev_[0].nsl), NTB, 0, s>>>(A0_, x_, b_, r_, nullptr, nullptr);
     k_r0<<<RED_BLOCKS, RED_NT, 0, s>>>(r_, N0(), partials_, st_);
     launch_precond(s, true);
     k_loop_ctl<<<1, 1, 0, s>>>(st_);
   }
 
   void launch_body(cudaStream_t s) {
-    k_spmv<double, B, 2><<<g0(), NTB, 0, s>>>(A0_, p_, nullptr, q_, partials_, st_);
+    k_spmv<double, B, 2><<<bgrid(k_spmv<double, B, 2>, lev_[0].nsl), NTB, 0, s>>>(A0_, p_, nullptr, q_, partials_, st_);
     k_cg_update<<<RED_BLOCKS, RED_NT, 0, s>>>(x_, r_, p_, q_, N0(), partials_, st_);
     launch_precond(s, false);
     k_loop_ctl<<<1, 1, 0, s>>>(st_);
@@ -235,7 +250,7 @@ class Engine : public EngineBase {
   void launch_step_prologue(cudaStream_t s) {
     IonicParams ip{sp_.model, sp_.k, sp_.a, sp_.eps, sp_.gamma, sp_.mu1, sp_.mu2};
     const double c = sp_.chi * sp_.cm / sp_.dt;
-    k_ionic_rhs<B><<<g0(), NTB, 0, s>>>(Me_, x_, w_, mask_, b_, ip, sp_.dt, sp_.chi, c, sp_.iapp_value,
+    k_ionic_rhs<B><<<bgrid(k_ionic_rhs<B>, lev_[0].nsl), NTB, 0, s>>>(Me_, x_, w_, mask_, b_, ip, sp_.dt, sp_.chi, c, sp_.iapp_value,
                                        sp_.iapp_steps, step_, lev_[0].nsl);
   }
 
@@ -327,6 +342,11 @@ class Engine : public EngineBase {
     (void)precision;
     nlev_ = h.L;
     degree_ = 3;
+    {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&num_sms_, cudaDevAttrMultiProcessorCount, dev);
+    }
     lev_.assign(nlev_, Lev());
     AGG_CK(cudaStreamCreateWithFlags(&cs_, cudaStreamNonBlocking));
     AGG_CK(cudaMallocHost(&st_host_, sizeof(CGState)));
@@ -486,12 +506,12 @@ class Engine : public EngineBase {
     const int64_t g = cdiv(v.n * B, 256);
     if (l == 0) {
       k_gather_units<double, double><<<g, 256, 0, s>>>(x_user, p_, v.perm, v.n, B);
-      k_spmv<double, B, 0><<<g0(), NTB, 0, s>>>(A0_, p_, nullptr, q_, nullptr, nullptr);
+      k_spmv<double, B, 0><<<bgrid(k_spmv<double, B, 0>, v.nsl), NTB, 0, s>>>(A0_, p_, nullptr, q_, nullptr, nullptr);
       k_scatter_units<double, double><<<g, 256, 0, s>>>(q_, y_user, v.perm, v.n, B);
     } else {
       if (l == nlev_ - 1) { err = "the coarsest level is applied through its Cholesky factor only"; return AGG_EUNSUPPORTED; }
       k_gather_units<T, double><<<g, 256, 0, s>>>(x_user, v.xa, v.perm, v.n, B);
-      k_spmv<T, B, 0><<<cdiv(v.nsl * SL, NTB), NTB, 0, s>>>(v.A(), v.xa, nullptr, v.xb, nullptr, nullptr);
+      k_spmv<T, B, 0><<<bgrid(k_spmv<T, B, 0>, v.nsl), NTB, 0, s>>>(v.A(), v.xa, nullptr, v.xb, nullptr, nullptr);
       k_scatter_units<double, T><<<g, 256, 0, s>>>(v.xb, y_user, v.perm, v.n, B);
     }
     AGG_CK(cudaGetLastError());
@@ -525,13 +545,13 @@ class Engine : public EngineBase {
       double* xi = static_cast<double*>(s_in);
       double* yi = static_cast<double*>(s_out);
       k_gather_units<double, double><<<g, 256, 0, s>>>(x_user, xi, v.perm, v.n, B);
-      k_spmv<double, B, 0><<<g0(), NTB, 0, s>>>(A0_, xi, nullptr, yi, nullptr, nullptr);
+      k_spmv<double, B, 0><<<bgrid(k_spmv<double, B, 0>, v.nsl), NTB, 0, s>>>(A0_, xi, nullptr, yi, nullptr, nullptr);
       k_scatter_units<double, double><<<g, 256, 0, s>>>(yi, y_user, v.perm, v.n, B);
     } else {
       T* xi = static_cast<T*>(s_in);
       T* yi = static_cast<T*>(s_out);
       k_gather_units<T, double><<<g, 256, 0, s>>>(x_user, xi, v.perm, v.n, B);
-      k_spmv<T, B, 0><<<cdiv(v.nsl * SL, NTB), NTB, 0, s>>>(v.A(), xi, nullptr, yi, nullptr, nullptr);
+      k_spmv<T, B, 0><<<bgrid(k_spmv<T, B, 0>, v.nsl), NTB, 0, s>>>(v.A(), xi, nullptr, yi, nullptr, nullptr);
       k_scatter_units<double, T><<<g, 256, 0, s>>>(yi, y_user, v.perm, v.n, B);
     }
     AGG_CK(cudaGetLastError());
@@ -613,15 +633,22 @@ class Engine : public EngineBase {
 
   int kernel_loop(int id, int reps, cudaStream_t s, std::string& err) override {
     Lev& v = lev_[0];
-    const int64_t g = g0();
+    const int64_t n = v.nsl;
     for (int i = 0; i < reps; ++i) {
       switch (id) {
-        case 0: k_spmv<double, B, 0><<<g, NTB, 0, s>>>(A0_, p_, nullptr, q_, nullptr, nullptr); break;
-        case 1:
-          k_cheb<T, TD, B, 2><<<g, NTB, 0, s>>>(v.A(), v.Dinv, v.rhs, v.xa, v.xb, v.d, v.c1[1], v.c2[1], v.nsl, nullptr);
+        case 0:
+          k_spmv<double, B, 0><<<bgrid(k_spmv<double, B, 0>, n), NTB, 0, s>>>(A0_, p_, nullptr, q_, nullptr, nullptr);
           break;
-        case 2: k_resid_restrict<T, B><<<g, NTB, 0, s>>>(v.A(), v.P, v.rhs, v.xa, v.S, nullptr); break;
-        case 3: k_prolong<T, B><<<g, NTB, 0, s>>>(v.P, v.parent, lev_[1].xa, v.xb, v.nsl, nullptr); break;
+        case 1:
+          k_cheb<T, TD, B, 2><<<bgrid(k_cheb<T, TD, B, 2>, n), NTB, 0, s>>>(v.A(), v.Dinv, v.rhs, v.xa, v.xb, v.d,
+                                                                          v.c1[1], v.c2[1], v.nsl, nullptr);
+          break;
+        case 2:
+          k_resid_restrict<T, B><<<bgrid(k_resid_restrict<T, B>, n), NTB, 0, s>>>(v.A(), v.P, v.rhs, v.xa, v.S, nullptr);
+          break;
+        case 3:
+          k_prolong<T, B><<<bgrid(k_prolong<T, B>, n), NTB, 0, s>>>(v.P, v.parent, lev_[1].xa, v.xb, v.nsl, nullptr);
+          break;
         default: err = "unknown kernel id"; return AGG_EINVAL;
       }
     }
@@ -665,8 +692,8 @@ class Engine : public EngineBase {
     k_gather_units<double, double><<<g, 256, 0, s>>>(wbar, wb_, v0.perm, v0.n, B);
     IonicParams ip{sp_.model, sp_.k, sp_.a, sp_.eps, sp_.gamma, sp_.mu1, sp_.mu2};
     const double c = sp_.chi * sp_.cm / sp_.dt;
-    k_adj_pointwise<B><<<g0(), NTB, 0, s>>>(Me_, x_, ua_, wa_, b_, wb_, ip, sp_.dt, sp_.chi, c, v0.nsl);
-    k_grad_logD<B><<<g0(), NTB, 0, s>>>(A0_, Ke_, Y_, x_, ub_, v0.perm, grad, v0.n);
+    k_adj_pointwise<B><<<bgrid(k_adj_pointwise<B>, v0.nsl), NTB, 0, s>>>(Me_, x_, ua_, wa_, b_, wb_, ip, sp_.dt, sp_.chi, c, v0.nsl);
+    k_grad_logD<B><<<bgrid(k_grad_logD<B>, v0.nsl), NTB, 0, s>>>(A0_, Ke_, Y_, x_, ub_, v0.perm, grad, v0.n);
     k_scatter_units<double, double><<<g, 256, 0, s>>>(b_, ubar, v0.perm, v0.n, B);
     k_scatter_units<double, double><<<g, 256, 0, s>>>(wb_, wbar, v0.perm, v0.n, B);
     AGG_CK(cudaMemcpyAsync(st_host_, st_, sizeof(CGState), cudaMemcpyDeviceToHost, s));

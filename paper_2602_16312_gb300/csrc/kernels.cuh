@@ -164,6 +164,18 @@ __device__ __forceinline__ void block_mtv_out(const TS* base, int lane, const A*
   }
 }
 
+// Unit kernels loop over slices (one warp per slice at a time); the host
+// sizes the grid so that every warp gets the same number of slices and all
+// warps are resident at once (no partial last wave).
+template <int NTB>
+__device__ __forceinline__ int64_t first_slice() {
+  return (int64_t)blockIdx.x * (NTB / 32) + (threadIdx.x >> 5);
+}
+template <int NTB>
+__device__ __forceinline__ int64_t slice_stride() {
+  return (int64_t)gridDim.x * (NTB / 32);
+}
+
 template <typename T>
 struct SellView {
   const int32_t* slice_ptr;   // [nslices + 1] slot offsets
@@ -271,11 +283,10 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
            CGState* st) {
   constexpr int NTB = UnitThreads<B>::value;
   if (st && st->done) return;
-  const int64_t unit = (int64_t)blockIdx.x * NTB + threadIdx.x;
-  const int64_t slice = unit / SL;
   const int lane = threadIdx.x & 31;
   double part = 0.0;
-  if (slice < A.nslices) {
+  for (int64_t slice = first_slice<NTB>(); slice < A.nslices; slice += slice_stride<NTB>()) {
+    const int64_t unit = slice * SL + lane;
     T acc[B];
 #pragma unroll
     for (int r = 0; r < B; ++r) acc[r] = T(0);
@@ -316,10 +327,9 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
   constexpr int NTB = UnitThreads<B>::value;
   if (st && st->done) return;
   constexpr int KPD = Pad<TD, B>::KP;
-  const int64_t unit = (int64_t)blockIdx.x * NTB + threadIdx.x;
-  const int64_t slice = unit / SL;
   const int lane = threadIdx.x & 31;
-  if (slice >= nslices) return;
+  for (int64_t slice = first_slice<NTB>(); slice < nslices; slice += slice_stride<NTB>()) {
+  const int64_t unit = slice * SL + lane;
   const size_t o = (size_t)unit * B;
   const TD* Db = Dinv + (size_t)slice * SL * KPD;
   T s[B];
@@ -362,6 +372,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
     d[o + r] = dn;
     x_new[o + r] = (KIND == 0) ? dn : x_old[o + r] + dn;
   }
+  }
 }
 
 // ---------------------------------------------------------------- transfers
@@ -373,10 +384,9 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
   constexpr int NTB = UnitThreads<B>::value;
   if (st && st->done) return;
   constexpr int KP = Pad<T, B>::KP;
-  const int64_t unit = (int64_t)blockIdx.x * NTB + threadIdx.x;
-  const int64_t slice = unit / SL;
   const int lane = threadIdx.x & 31;
-  if (slice >= A.nslices) return;
+  for (int64_t slice = first_slice<NTB>(); slice < A.nslices; slice += slice_stride<NTB>()) {
+  const int64_t unit = slice * SL + lane;
   const size_t o = (size_t)unit * B;
   const T* Pb = P + (size_t)slice * SL * KP;
   T s[B];
@@ -390,7 +400,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
 #pragma unroll
     for (int r = 0; r < B; ++r) acc[r] = rhs[o + r] - acc[r];
     block_mtv_out<T, T, B>(Pb, lane, acc, S + o);
-    return;
+    continue;
   } else {
     T acc[B];
 #pragma unroll
@@ -403,6 +413,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
   }
 #pragma unroll
   for (int j = 0; j < B; ++j) S[o + j] = s[j];
+  }
 }
 
 // rc[K*B + j] = sum over the children u of K of S[u*B + j] (children contiguous)
@@ -427,10 +438,9 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
   constexpr int NTB = UnitThreads<B>::value;
   if (st && st->done) return;
   constexpr int KP = Pad<T, B>::KP;
-  const int64_t unit = (int64_t)blockIdx.x * NTB + threadIdx.x;
-  const int64_t slice = unit / SL;
   const int lane = threadIdx.x & 31;
-  if (slice >= nslices) return;
+  for (int64_t slice = first_slice<NTB>(); slice < nslices; slice += slice_stride<NTB>()) {
+  const int64_t unit = slice * SL + lane;
   const size_t o = (size_t)unit * B;
   const T* eb = ec + (size_t)parent[unit] * B;
   T acc[B];
@@ -446,6 +456,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
   }
 #pragma unroll
   for (int r = 0; r < B; ++r) x[o + r] += acc[r];
+  }
 }
 
 // ---------------------------------------------------------------- coarsest solve
