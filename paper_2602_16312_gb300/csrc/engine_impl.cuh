@@ -66,11 +66,38 @@ class Engine : public EngineBase {
 
   // Grid of a slice-looping unit kernel: one slice per warp. (Sizing the grid
   // to the resident warps and looping removes the partial last wave, but the
-  // lower concurrency cost more bandwidth than the tail on GB300: measured.)
+  // lower concurrency cost more bandwidth than the tail saved on GB300.)
   template <typename K>
   int64_t bgrid(K, int64_t nsl) const {
     return std::max<int64_t>(1, cdiv(nsl * SL, NTB));
   }
+  int nlev_ = 0, degree_ = 3;
+  SellView<double> A0_{};
+  double* Me_ = nullptr;
+  double *Linv_ = nullptr, *U_ = nullptr, *yc_ = nullptr;
+  int64_t nc_ = 0;
+  double *b_ = nullptr, *x_ = nullptr, *r_ = nullptr, *p_ = nullptr, *q_ = nullptr, *z_ = nullptr;
+  double* partials_ = nullptr;
+  float* r32_ = nullptr;
+  CGState* st_ = nullptr;
+  CGState* st_host_ = nullptr;
+  std::vector<void*> allocs_;
+  cudaStream_t cs_ = nullptr;
+  bool use_cond_ = false;
+  // solve graphs
+  cudaGraphExec_t solve_exec_ = nullptr, init_exec_ = nullptr, body_exec_ = nullptr;
+  std::vector<cudaGraph_t> graphs_;
+  // simulation
+  bool sim_ = false;
+  SimParams sp_{};
+  double *w_ = nullptr, *mask_ = nullptr;
+  int64_t* step_ = nullptr;
+  int *iters_ = nullptr, *slot_ = nullptr, *sim_status_ = nullptr;
+  int cap_ = 1024;
+  // adjoint data and buffers
+  double *Ke_ = nullptr, *Y_ = nullptr;
+  double *ua_ = nullptr, *wa_ = nullptr, *ub_ = nullptr, *wb_ = nullptr;
+  cudaGraphExec_t step_exec_ = nullptr, step_pro_exec_ = nullptr, step_epi_exec_ = nullptr;
 
   template <typename X>
   int dalloc(X** p, size_t count, std::string& err) {
