@@ -37,6 +37,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="f32", choices=["f32", "f64", "bf16s"])
+    ap.add_argument("--fine", default="bsr", choices=["bsr", "mf"],
+                    help="V-cycle level-0 operator: assembled blocks or matrix-free")
     ap.add_argument("--workload", default="jsquare2d", choices=list(WORKLOADS))
     ap.add_argument("--n", type=int, default=None, help="elements per direction (box workloads)")
     ap.add_argument("--e2e-steps", type=int, default=10)
@@ -192,7 +194,7 @@ def run_ours(args, rank, world):
     wl = workload(args)
     t0 = time.time()
     mesh = aggmg.Mesh.from_workload(wl)
-    hier = aggmg.Hierarchy(mesh, 1.0 / wl.dt, wl.maps, precision=args.form)
+    hier = aggmg.Hierarchy(mesh, 1.0 / wl.dt, wl.maps, precision=args.form, fine=args.fine)
     setup_s = time.time() - t0
     if args.profile_kernel is not None:
         hier.profile_kernel(args.profile_kernel, 3)
@@ -292,7 +294,8 @@ def run_ours(args, rank, world):
                                      "bf16s": "f32 V-cycle with bf16-stored smoother blocks"}[args.form],
         "data": "synthetic",
         "mdof_per_s": N * total_steps / t / 1e6,
-        "config": {"workload": workload_name(wl), "form": args.form, "parallelism": f"replicas x{world}",
+        "config": {"workload": workload_name(wl), "form": args.form, "fine_operator": args.fine,
+                   "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2 (fine float64 matrix {k0bytes / 1e9:.2f} GB, 129 MB L2)",
                    "levels": st["units"], "op_complexity": st["op_complexity"], "setup_s": setup_s,
                    "conditional_graph": os.environ.get("AGG_NO_COND_GRAPH") is None, "flexible_cg": flexible},

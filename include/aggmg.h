@@ -112,6 +112,13 @@ typedef struct {
   double cheb_upper_safety;      /* lambda_max = safety * Ritz max (default 1.2) */
   double cheb_range;             /* lambda_min = lambda_max / range (default 20) */
   int vcycle_precision;          /* AGG_F64, AGG_F32 or AGG_F32_BF16SMOOTH       */
+  int fine_operator;             /* V-cycle's level-0 operator: 0 assembled
+                                    blocks; 1 matrix-free (the SIPG form and
+                                    mass term evaluated from quadrature data
+                                    with sum factorisation, Section 5.2); 1
+                                    needs a 2D mesh with p <= 3, quad_extra 1
+                                    and a float32 V-cycle. The outer CG always
+                                    uses the assembled float64 operator.     */
 } agg_mg_opts;
 
 void agg_mg_opts_default(agg_mg_opts* opts);
@@ -157,7 +164,9 @@ typedef struct {
 agg_status agg_pcg_solve(agg_hier_t hier, const double* b_dev, double* x_dev,
                          const agg_pcg_opts* opts, agg_pcg_result* res, void* stream);
 /* y = A_l x with the level's stored operator (float64 on level 0 always;
- * levels >= 1 in the V-cycle precision, converted from/to float64). */
+ * levels >= 1 in the V-cycle precision, converted from/to float64).
+ * level = -1: the V-cycle's level-0 operator in the V-cycle precision (the
+ * matrix-free one when fine_operator = 1). */
 agg_status agg_operator_apply(agg_hier_t hier, int level, const double* x_dev, double* y_dev,
                               void* stream);
 /* z = B r: one V-cycle of the preconditioner (Section 6). */

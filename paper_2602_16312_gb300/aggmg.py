@@ -38,7 +38,8 @@ class MeshDesc(C.Structure):
 class MGOpts(C.Structure):
     _fields_ = [("n_levels", C.c_int), ("agg_maps", C.POINTER(C.POINTER(C.c_int32))),
                 ("smoother_degree", C.c_int), ("block_jacobi", C.c_int), ("lanczos_steps", C.c_int),
-                ("cheb_upper_safety", C.c_double), ("cheb_range", C.c_double), ("vcycle_precision", C.c_int)]
+                ("cheb_upper_safety", C.c_double), ("cheb_range", C.c_double), ("vcycle_precision", C.c_int),
+                ("fine_operator", C.c_int)]
 
 
 class PCGOpts(C.Structure):
@@ -231,8 +232,11 @@ class Mesh:
             pass
 
 
+FINE_OPERATORS = {"bsr": 0, "mf": 1}
+
+
 def _mg_opts(maps: Sequence[np.ndarray], precision="f64", block_jacobi=True, lanczos_steps=12,
-             safety=1.2, cheb_range=20.0):
+             safety=1.2, cheb_range=20.0, fine="bsr"):
     o = MGOpts()
     lib().agg_mg_opts_default(C.byref(o))
     keep = [np.ascontiguousarray(m, dtype=np.int32) for m in maps]
@@ -246,6 +250,7 @@ def _mg_opts(maps: Sequence[np.ndarray], precision="f64", block_jacobi=True, lan
     o.cheb_upper_safety = safety
     o.cheb_range = cheb_range
     o.vcycle_precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.fine_operator = FINE_OPERATORS[fine] if isinstance(fine, str) else int(fine)
     return o, (keep, arr)
 
 

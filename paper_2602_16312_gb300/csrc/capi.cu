@@ -185,6 +185,7 @@ void agg_mg_opts_default(agg_mg_opts* o) {
   o->cheb_upper_safety = 1.2;
   o->cheb_range = 20.0;
   o->vcycle_precision = AGG_F64;
+  o->fine_operator = 0;
 }
 
 static agg_status check_mg_opts(const agg_mg_opts* o, double mass_coeff);
@@ -218,7 +219,7 @@ agg_status agg_mg_hierarchy_setup(agg_mesh_t mesh, double mass_coeff, const agg_
       h->lam_max.push_back(hh.lev[l].lam_max);
     }
     h->perm0 = hh.lev[0].perm;
-    s = eng->init(hh, m, o->vcycle_precision, (cudaStream_t)stream, err);
+    s = eng->init(hh, m, o->vcycle_precision, o->fine_operator, (cudaStream_t)stream, err);
     if (s) return fail((agg_status)s, err);
   } catch (const std::bad_alloc&) {
     return fail(AGG_ENOMEM, "host allocation failed");
@@ -264,6 +265,7 @@ static agg_status check_mg_opts(const agg_mg_opts* o, double mass_coeff) {
   if (!(o->cheb_upper_safety > 0) || !(o->cheb_range > 1) || o->lanczos_steps < 1)
     return fail(AGG_EINVAL, "Chebyshev options");
   if (!(mass_coeff >= 0) || !std::isfinite(mass_coeff)) return fail(AGG_EINVAL, "mass_coeff");
+  if (o->fine_operator != 0 && o->fine_operator != 1) return fail(AGG_EINVAL, "fine_operator");
   return AGG_OK;
 }
 

@@ -33,7 +33,8 @@ class EngineBase {
  public:
   virtual ~EngineBase() {}
   // upload the host hierarchy (and element mass blocks) and capture graphs
-  virtual int init(const HostHierarchy& h, const Mesh& m, int precision, cudaStream_t s, std::string& err) = 0;
+  virtual int init(const HostHierarchy& h, const Mesh& m, int precision, int fine_operator, cudaStream_t s,
+                   std::string& err) = 0;
   virtual int pcg_solve(const double* b_user, double* x_user, const SolveOpts& o, SolveResult& res,
                         cudaStream_t s, std::string& err) = 0;
   virtual int apply_level(int level, const double* x_user, double* y_user, cudaStream_t s, std::string& err) = 0;

@@ -19,6 +19,7 @@
 #include "cg_kernels.cuh"
 #include "engine.h"
 #include "kernels.cuh"
+#include "mf_kernels.cuh"
 
 namespace aggmg {
 
@@ -45,6 +46,12 @@ inline __nv_bfloat16 to_storage<__nv_bfloat16>(double v) {
 template <typename T, typename TD, int B>
 class Engine : public EngineBase {
   static constexpr int NTB = UnitThreads<B>::value;
+  // matrix-free fine operator: float32 V-cycle on 2D elements of p = 1..3
+  static constexpr bool kMf = std::is_same<T, float>::value && (B == 4 || B == 9 || B == 16);
+  using MfOpT = typename std::conditional<kMf, MfOp<kMf ? B : 9>, SellOp<T, B>>::type;
+  bool mf_ = false;
+  MfOpT mfop_{};
+  int64_t mf_bytes_ = 0;
   struct Lev {
     int64_t n = 0, nsl = 0, nvec = 0;
     int32_t* slice_ptr = nullptr;
@@ -185,31 +192,41 @@ class Engine : public EngineBase {
       k_coarse_upper<T><<<g, 256, 0, s>>>(U_, yc_, v.xa, nc_, st_);
       return v.xa;
     }
+    if constexpr (kMf) {
+      if (l == 0 && mf_) return vc_level(l, mfop_, s);
+    }
+    return vc_level(l, SellOp<T, B>{v.A()}, s);
+  }
+
+  // One level of the V-cycle with the level operator `op` (assembled blocks
+  // or the matrix-free fine operator).
+  template <typename Op>
+  T* vc_level(int l, const Op& op, cudaStream_t s) {
+    Lev& v = lev_[l];
     T* xo = v.xa;
     T* xn = v.xb;
-    const SellView<T> A = v.A();
-    const int64_t g0k = bgrid(k_cheb<T, TD, B, 0>, v.nsl), g1k = bgrid(k_cheb<T, TD, B, 1>, v.nsl);
-    const int64_t g2k = bgrid(k_cheb<T, TD, B, 2>, v.nsl);
-    k_cheb<T, TD, B, 0><<<g0k, NTB, 0, s>>>(A, v.Dinv, v.rhs, nullptr, xo, v.d, T(0), v.c2[0], v.nsl, st_);
+    const int64_t g = bgrid(0, v.nsl);
+    k_cheb<T, TD, B, 0, Op><<<g, NTB, 0, s>>>(op, v.Dinv, v.rhs, nullptr, xo, v.d, T(0), v.c2[0], v.nsl, st_);
     for (int k = 1; k < degree_; ++k) {
-      k_cheb<T, TD, B, 2><<<g2k, NTB, 0, s>>>(A, v.Dinv, v.rhs, xo, xn, v.d, v.c1[k], v.c2[k], v.nsl, st_);
+      k_cheb<T, TD, B, 2, Op><<<g, NTB, 0, s>>>(op, v.Dinv, v.rhs, xo, xn, v.d, v.c1[k], v.c2[k], v.nsl, st_);
       std::swap(xo, xn);
     }
     Lev& c = lev_[l + 1];
-    k_resid_restrict<T, B><<<bgrid(k_resid_restrict<T, B>, v.nsl), NTB, 0, s>>>(A, v.P, v.rhs, xo, v.S, st_);
+    k_resid_restrict<T, B, Op><<<g, NTB, 0, s>>>(op, v.P, v.rhs, xo, v.S, st_);
     k_segsum<T, B><<<cdiv(c.n * B, 256), 256, 0, s>>>(c.child_ptr, v.S, c.rhs, c.n, st_);
     T* ec = vc(l + 1, s);
-    k_prolong<T, B><<<bgrid(k_prolong<T, B>, v.nsl), NTB, 0, s>>>(v.P, v.parent, ec, xo, v.nsl, st_);
-    k_cheb<T, TD, B, 1><<<g1k, NTB, 0, s>>>(A, v.Dinv, v.rhs, xo, xn, v.d, T(0), v.c2[0], v.nsl, st_);
+    k_prolong<T, B><<<g, NTB, 0, s>>>(v.P, v.parent, ec, xo, v.nsl, st_);
+    k_cheb<T, TD, B, 1, Op><<<g, NTB, 0, s>>>(op, v.Dinv, v.rhs, xo, xn, v.d, T(0), v.c2[0], v.nsl, st_);
     std::swap(xo, xn);
     for (int k = 1; k < degree_; ++k) {
-      k_cheb<T, TD, B, 2><<<g2k, NTB, 0, s>>>(A, v.Dinv, v.rhs, xo, xn, v.d, v.c1[k], v.c2[k], v.nsl, st_);
+      k_cheb<T, TD, B, 2, Op><<<g, NTB, 0, s>>>(op, v.Dinv, v.rhs, xo, xn, v.d, v.c1[k], v.c2[k], v.nsl, st_);
       std::swap(xo, xn);
     }
     return xo;
   }
 
   int64_t N0() const { return lev_[0].nvec; }
+  bool use_mf0() const { return kMf && mf_; }
   int64_t g0() const { return cdiv(lev_[0].nsl * SL, NTB); }
 
   void launch_precond(cudaStream_t s, bool init) {
@@ -333,7 +350,8 @@ class Engine : public EngineBase {
 
   bool uses_conditional_graph() const override { return use_cond_; }
 
-  int init(const HostHierarchy& h, const Mesh& m, int precision, cudaStream_t s, std::string& err) override {
+  int init(const HostHierarchy& h, const Mesh& m, int precision, int fine_operator, cudaStream_t s,
+           std::string& err) override {
     (void)precision;
     nlev_ = h.L;
     degree_ = 3;
@@ -434,6 +452,42 @@ class Engine : public EngineBase {
       }
       if ((rc = upload(&Y_, hy.data(), hy.size(), err))) return rc;
     }
+    // matrix-free fine operator for the float32 V-cycle (2D)
+    if (fine_operator == 1) {
+      if constexpr (kMf) {
+        MatrixFreeData md;
+        if ((rc = matrix_free_build(m, h.lev[0].perm, h.lev[0].inv, h.mass_coeff, md, err))) return rc;
+        if (md.q != MfDegree<kMf ? B : 9>::value + 2) { err = "matrix-free operator needs quad_extra = 1"; return AGG_EUNSUPPORTED; }
+        float *cell, *face;
+        int32_t* nbr;
+        int8_t* code;
+        if ((rc = upload(&cell, md.cell.data(), md.cell.size(), err))) return rc;
+        if ((rc = upload(&face, md.face.data(), md.face.size(), err))) return rc;
+        if ((rc = upload(&nbr, md.nbr.data(), md.nbr.size(), err))) return rc;
+        if ((rc = upload(&code, md.code.data(), md.code.size(), err))) return rc;
+        mfop_.V = MfView{cell, face, nbr, code, lev_[0].nsl};
+        Tables1D t1 = make_tables(m.p, md.q);
+        std::memset(&mfop_.T, 0, sizeof(mfop_.T));
+        for (int a = 0; a <= m.p; ++a) {
+          for (int kq = 0; kq < md.q; ++kq) {
+            double v[8], dv[8];
+            lagrange_eval(t1.gll.data(), m.p + 1, t1.gx[kq], v, dv);
+            mfop_.T.L[a][kq] = (float)v[a];
+            mfop_.T.D[a][kq] = (float)dv[a];
+          }
+          for (int sd = 0; sd < 2; ++sd) {
+            double v[8], dv[8];
+            lagrange_eval(t1.gll.data(), m.p + 1, (double)sd, v, dv);
+            mfop_.T.Dend[sd][a] = (float)dv[a];
+          }
+        }
+        mf_bytes_ = (int64_t)(md.cell.size() * 4 + md.face.size() * 4 + md.nbr.size() * 4 + md.code.size());
+        mf_ = true;
+      } else {
+        err = "the matrix-free fine operator needs a 2D mesh (p <= 3) and a float32 V-cycle";
+        return AGG_EUNSUPPORTED;
+      }
+    }
     // coarsest: inverse Cholesky factor and its transpose
     nc_ = h.nc;
     {
@@ -496,6 +550,19 @@ class Engine : public EngineBase {
   }
 
   int apply_level(int l, const double* x_user, double* y_user, cudaStream_t s, std::string& err) override {
+    if (l == -1) {
+      // the V-cycle's level-0 operator in its own precision (matrix-free if selected)
+      Lev& v = lev_[0];
+      const int64_t g = cdiv(v.n * B, 256);
+      k_gather_units<T, double><<<g, 256, 0, s>>>(x_user, v.xa, v.perm, v.n, B);
+      if (use_mf0())
+        k_op_apply<T, B, MfOpT><<<bgrid(0, v.nsl), NTB, 0, s>>>(mfop_, v.xa, v.xb);
+      else
+        k_op_apply<T, B, SellOp<T, B>><<<bgrid(0, v.nsl), NTB, 0, s>>>(SellOp<T, B>{v.A()}, v.xa, v.xb);
+      k_scatter_units<double, T><<<g, 256, 0, s>>>(v.xb, y_user, v.perm, v.n, B);
+      AGG_CK(cudaGetLastError());
+      return AGG_OK;
+    }
     if (l < 0 || l >= nlev_) { err = "level out of range"; return AGG_EINVAL; }
     Lev& v = lev_[l];
     const int64_t g = cdiv(v.n * B, 256);
@@ -635,11 +702,19 @@ class Engine : public EngineBase {
           k_spmv<double, B, 0><<<bgrid(k_spmv<double, B, 0>, n), NTB, 0, s>>>(A0_, p_, nullptr, q_, nullptr, nullptr);
           break;
         case 1:
-          k_cheb<T, TD, B, 2><<<bgrid(k_cheb<T, TD, B, 2>, n), NTB, 0, s>>>(v.A(), v.Dinv, v.rhs, v.xa, v.xb, v.d,
-                                                                          v.c1[1], v.c2[1], v.nsl, nullptr);
+          if (use_mf0())
+            k_cheb<T, TD, B, 2, MfOpT><<<bgrid(0, n), NTB, 0, s>>>(mfop_, v.Dinv, v.rhs, v.xa, v.xb, v.d, v.c1[1],
+                                                                   v.c2[1], v.nsl, nullptr);
+          else
+            k_cheb<T, TD, B, 2, SellOp<T, B>><<<bgrid(0, n), NTB, 0, s>>>(SellOp<T, B>{v.A()}, v.Dinv, v.rhs, v.xa,
+                                                                          v.xb, v.d, v.c1[1], v.c2[1], v.nsl, nullptr);
           break;
         case 2:
-          k_resid_restrict<T, B><<<bgrid(k_resid_restrict<T, B>, n), NTB, 0, s>>>(v.A(), v.P, v.rhs, v.xa, v.S, nullptr);
+          if (use_mf0())
+            k_resid_restrict<T, B, MfOpT><<<bgrid(0, n), NTB, 0, s>>>(mfop_, v.P, v.rhs, v.xa, v.S, nullptr);
+          else
+            k_resid_restrict<T, B, SellOp<T, B>><<<bgrid(0, n), NTB, 0, s>>>(SellOp<T, B>{v.A()}, v.P, v.rhs, v.xa,
+                                                                             v.S, nullptr);
           break;
         case 3:
           k_prolong<T, B><<<bgrid(k_prolong<T, B>, n), NTB, 0, s>>>(v.P, v.parent, lev_[1].xa, v.xb, v.nsl, nullptr);
@@ -656,8 +731,14 @@ class Engine : public EngineBase {
     const double sT = sizeof(T), sD = sizeof(TD);
     switch (id) {
       case 0: bytes = nz * (bb * 8 + 4) + 2 * N * 8; flops = 2 * nz * bb; break;
-      case 1: bytes = nz * (bb * sT + 4) + n0 * bb * sD + 5 * N * sT; flops = 2 * nz * bb + 2 * n0 * bb + 4 * N; break;
-      case 2: bytes = nz * (bb * sT + 4) + n0 * bb * sT + 3 * N * sT; flops = 2 * nz * bb + 2 * n0 * bb + N; break;
+      case 1:
+        bytes = (use_mf0() ? (double)mf_bytes_ : nz * (bb * sT + 4)) + n0 * bb * sD + 5 * N * sT;
+        flops = 2 * nz * bb + 2 * n0 * bb + 4 * N;
+        break;
+      case 2:
+        bytes = (use_mf0() ? (double)mf_bytes_ : nz * (bb * sT + 4)) + n0 * bb * sT + 3 * N * sT;
+        flops = 2 * nz * bb + 2 * n0 * bb + N;
+        break;
       case 3: bytes = n0 * bb * sT + 2 * N * sT + (double)lev_[1].n * B * sT + n0 * 4; flops = 2 * n0 * bb + N; break;
       default: return AGG_EINVAL;
     }

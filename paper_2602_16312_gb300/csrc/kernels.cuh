@@ -320,9 +320,9 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
 // KIND 2: d = c1 d + c2 Dinv (rhs - A x_old), x_new = x_old + d
 // Blocks of more than 32 DoFs keep the residual in the thread's own strided
 // shared-memory slot (read by that thread only) instead of registers.
-template <typename T, typename TD, int B, int KIND>
+template <typename T, typename TD, int B, int KIND, typename Op>
 static __global__ void __launch_bounds__(UnitThreads<B>::value)
-    k_cheb(SellView<T> A, const TD* __restrict__ Dinv, const T* __restrict__ rhs, const T* __restrict__ x_old,
+    k_cheb(Op A, const TD* __restrict__ Dinv, const T* __restrict__ rhs, const T* __restrict__ x_old,
            T* __restrict__ x_new, T* __restrict__ d, T c1, T c2, int64_t nslices, const CGState* st) {
   constexpr int NTB = UnitThreads<B>::value;
   if (st && st->done) return;
@@ -345,7 +345,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
         T acc[B];
 #pragma unroll
         for (int r = 0; r < B; ++r) acc[r] = T(0);
-        sell_row<T, B>(A, slice, lane, x_old, acc);
+        A.apply(slice, lane, x_old, acc);
 #pragma unroll
         for (int r = 0; r < B; ++r) ts[r * NTB] = rhs[o + r] - acc[r];
       }
@@ -360,7 +360,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
       T acc[B];
 #pragma unroll
       for (int r = 0; r < B; ++r) acc[r] = T(0);
-      sell_row<T, B>(A, slice, lane, x_old, acc);
+      A.apply(slice, lane, x_old, acc);
 #pragma unroll
       for (int r = 0; r < B; ++r) t[r] = rhs[o + r] - acc[r];
     }
@@ -377,15 +377,15 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
 
 // ---------------------------------------------------------------- transfers
 // S_u = P_u^T (rhs_u - (A x)_u): residual of the pre-smoothed iterate, restricted
-template <typename T, int B>
+template <typename T, int B, typename Op>
 static __global__ void __launch_bounds__(UnitThreads<B>::value)
-    k_resid_restrict(SellView<T> A, const T* __restrict__ P, const T* __restrict__ rhs, const T* __restrict__ x,
+    k_resid_restrict(Op A, const T* __restrict__ P, const T* __restrict__ rhs, const T* __restrict__ x,
                      T* __restrict__ S, const CGState* st) {
   constexpr int NTB = UnitThreads<B>::value;
   if (st && st->done) return;
   constexpr int KP = Pad<T, B>::KP;
   const int lane = threadIdx.x & 31;
-  for (int64_t slice = first_slice<NTB>(); slice < A.nslices; slice += slice_stride<NTB>()) {
+  for (int64_t slice = first_slice<NTB>(); slice < A.nslices(); slice += slice_stride<NTB>()) {
   const int64_t unit = slice * SL + lane;
   const size_t o = (size_t)unit * B;
   const T* Pb = P + (size_t)slice * SL * KP;
@@ -396,7 +396,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
     T acc[B];
 #pragma unroll
     for (int r = 0; r < B; ++r) acc[r] = T(0);
-    sell_row<T, B>(A, slice, lane, x, acc);
+    A.apply(slice, lane, x, acc);
 #pragma unroll
     for (int r = 0; r < B; ++r) acc[r] = rhs[o + r] - acc[r];
     block_mtv_out<T, T, B>(Pb, lane, acc, S + o);
@@ -405,7 +405,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
     T acc[B];
 #pragma unroll
     for (int r = 0; r < B; ++r) acc[r] = T(0);
-    sell_row<T, B>(A, slice, lane, x, acc);
+    A.apply(slice, lane, x, acc);
     T t[B];
 #pragma unroll
     for (int r = 0; r < B; ++r) t[r] = rhs[o + r] - acc[r];

@@ -46,6 +46,11 @@ struct Mesh {
   // column n != e, the four blocks (ee, en, ne, nn) of the face terms built
   // with D_e; with Ke the volume form, sum_e of these parts is A.
   bool adjoint_data = false;
+  // face neighbours: face_nbr[e*2d + f] = n*2d + fn for an interior face, -1
+  // on the boundary; face_rev: 1 when the neighbour runs the shared face in
+  // the opposite direction (2D)
+  std::vector<int64_t> face_nbr;
+  std::vector<int8_t> face_rev;
   std::vector<double> Ke;        // [ne][B][B]
   std::vector<double> Y;         // [nnzb][4][B][B]
 };
@@ -92,6 +97,23 @@ struct HierOptions {
 
 int hierarchy_build(const Mesh& m, double mass_coeff, const HierOptions& o, HostHierarchy& h,
                     std::string& err);
+
+// Quadrature data of the matrix-free fine operator (2D), elements in the
+// order `perm` (internal -> element id), packed per slice of 32 elements:
+//   cell[slice][qp*4 + {G00, G01, G11, m}][lane]  with G = w |J| J^-1 D J^-T,
+//                                               m = c w |J|
+//   face[slice][f][q*5 + {a0, a1, b0, b1, s}][lane] with a = wdS J_e^-1 D_e n,
+//        b = wdS J_n^-1 D_n n (neighbour), s = wdS sigma  (n: e's outward normal)
+//   nbr[slice][f][lane]  neighbour's internal index or -1
+//   code[slice][f][lane] neighbour's local face * 2 + reversed
+struct MatrixFreeData {
+  int q = 0;
+  std::vector<float> cell, face;
+  std::vector<int32_t> nbr;
+  std::vector<int8_t> code;
+};
+int matrix_free_build(const Mesh& m, const std::vector<int64_t>& perm, const std::vector<int64_t>& inv, double c,
+                      MatrixFreeData& out, std::string& err);
 
 // y = A x on the host (block CSR, float64)
 void bsr_apply(const BlockCSR& A, const double* x, double* y);

@@ -337,6 +337,16 @@ int mesh_build(Mesh& m, std::string& err) {
     i = j;
   }
   m.n_faces = nint;
+  m.face_nbr = nbr;
+  m.face_rev.assign((size_t)ne * nf, 0);
+  for (int64_t e = 0; e < ne; ++e)
+    for (int f = 0; f < nf; ++f) {
+      const int64_t rec = nbr[e * nf + f];
+      if (rec < 0) continue;
+      const int64_t n = rec / nf;
+      const int fn = (int)(rec % nf);
+      m.face_rev[e * nf + f] = (int8_t)(m.cells[n * V + fcorn[fn][0]] != m.cells[e * V + fcorn[f][0]]);
+    }
 
   // ---------------- block rows: diagonal + one block per interior face
   m.A.nrows = ne;
@@ -591,6 +601,121 @@ void bsr_apply(const BlockCSR& A, const double* x, double* y) {
     }
     for (int i = 0; i < B; ++i) y[r * B + i] = acc[i];
   }
+}
+
+}  // namespace aggmg
+
+namespace aggmg {
+
+int matrix_free_build(const Mesh& m, const std::vector<int64_t>& perm, const std::vector<int64_t>& inv, double c,
+                      MatrixFreeData& out, std::string& err) {
+  if (m.dim != 2) { err = "the matrix-free fine operator is built for 2D meshes"; return AGG_EUNSUPPORTED; }
+  const int dim = 2, V = 4, nf = 4, p = m.p;
+  const int q = p + 1 + m.quad_extra;
+  const int Q = q * q;
+  const double c_pen = (m.penalty_mode == 0) ? double(p * (p + 1)) : m.penalty_coeff * p * p;
+  Tables1D t = make_tables(p, q);
+  const int64_t ne = m.ne;
+  const int64_t nsl = (ne + 31) / 32;
+  out.q = q;
+  out.cell.assign((size_t)nsl * 32 * Q * 4, 0.0f);
+  out.face.assign((size_t)nsl * 32 * nf * q * 5, 0.0f);
+  out.nbr.assign((size_t)nsl * 32 * nf, -1);
+  out.code.assign((size_t)nsl * 32 * nf, 0);
+  int fcorn[4][2];
+  for (int f = 0; f < nf; ++f) face_corners(dim, f, fcorn[f]);
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(+ : bad)
+  for (int64_t r = 0; r < ne; ++r) {
+    const int64_t e = perm[r];
+    const int64_t sl = r / 32, lane = r % 32;
+    double Xe[8], Xn[8];
+    for (int cc = 0; cc < V; ++cc)
+      for (int k = 0; k < dim; ++k) Xe[cc * dim + k] = m.X[m.cells[e * V + cc] * dim + k];
+    const double* De = &m.D[e * 4];
+    // cell quadrature: G = w |J| J^-1 D J^-T, m = c w |J|
+    for (int iq = 0; iq < Q; ++iq) {
+      double xi[2] = {t.gx[iq % q], t.gx[iq / q]};
+      const double w = t.gw[iq % q] * t.gw[iq / q];
+      double x[2], J[MAXD][MAXD], Ji[MAXD][MAXD];
+      map_point(dim, Xe, xi, x, J);
+      const double det = det_inv(dim, J, Ji);
+      if (!(det > 0)) bad += 1;
+      double G[2][2];
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+          double sacc = 0.0;
+          for (int k = 0; k < 2; ++k)
+            for (int l = 0; l < 2; ++l) sacc += Ji[a][k] * De[k * 2 + l] * Ji[b][l];
+          G[a][b] = w * det * sacc;
+        }
+      const double vals[4] = {G[0][0], G[0][1], G[1][1], c * w * det};
+      for (int comp = 0; comp < 4; ++comp)
+        out.cell[((size_t)sl * Q * 4 + iq * 4 + comp) * 32 + lane] = (float)vals[comp];
+    }
+    // faces
+    for (int f = 0; f < nf; ++f) {
+      const int64_t rec = m.face_nbr[e * nf + f];
+      if (rec < 0) continue;
+      const int64_t n = rec / nf;
+      const int fn = (int)(rec % nf);
+      const int rev = m.face_rev[e * nf + f];
+      out.nbr[((size_t)sl * nf + f) * 32 + lane] = (int32_t)inv[n];
+      out.code[((size_t)sl * nf + f) * 32 + lane] = (int8_t)(fn * 2 + rev);
+      for (int cc = 0; cc < V; ++cc)
+        for (int k = 0; k < dim; ++k) Xn[cc * dim + k] = m.X[m.cells[n * V + cc] * dim + k];
+      const double* Dn = &m.D[n * 4];
+      const int kf = f / 2, sf = f % 2, kn = fn / 2, sn = fn % 2;
+      double area = 0.0;
+      std::vector<double> a0(q), a1(q), b0(q), b1(q), sg(q), wdS(q);
+      for (int iq = 0; iq < q; ++iq) {
+        const double tq = t.gx[iq];
+        double xip[2], xim[2];
+        xip[kf] = sf;
+        xip[1 - kf] = tq;
+        xim[kn] = sn;
+        xim[1 - kn] = rev ? 1.0 - tq : tq;
+        double xp[2], xm[2], Jp[MAXD][MAXD], Jm[MAXD][MAXD], Jip[MAXD][MAXD], Jim[MAXD][MAXD];
+        map_point(dim, Xe, xip, xp, Jp);
+        map_point(dim, Xn, xim, xm, Jm);
+        const double detp = det_inv(dim, Jp, Jip);
+        det_inv(dim, Jm, Jim);
+        if (std::fabs(xp[0] - xm[0]) + std::fabs(xp[1] - xm[1]) > 1e-10 * (1.0 + std::fabs(xp[0]) + std::fabs(xp[1])))
+          bad += 1;
+        double nv[2], len = 0.0;
+        for (int k = 0; k < 2; ++k) {
+          nv[k] = Jip[kf][k] * (2.0 * sf - 1.0);
+          len += nv[k] * nv[k];
+        }
+        len = std::sqrt(len);
+        const double nn[2] = {nv[0] / len, nv[1] / len};
+        wdS[iq] = t.gw[iq] * detp * len;
+        area += wdS[iq];
+        double Den[2], Dnn[2];
+        for (int k = 0; k < 2; ++k) {
+          Den[k] = De[k * 2 + 0] * nn[0] + De[k * 2 + 1] * nn[1];
+          Dnn[k] = Dn[k * 2 + 0] * nn[0] + Dn[k * 2 + 1] * nn[1];
+        }
+        // a = wdS J_e^-1 D_e n (reference-gradient coefficients), b likewise on the neighbour
+        a0[iq] = wdS[iq] * (Jip[0][0] * Den[0] + Jip[0][1] * Den[1]);
+        a1[iq] = wdS[iq] * (Jip[1][0] * Den[0] + Jip[1][1] * Den[1]);
+        b0[iq] = wdS[iq] * (Jim[0][0] * Dnn[0] + Jim[0][1] * Dnn[1]);
+        b1[iq] = wdS[iq] * (Jim[1][0] * Dnn[0] + Jim[1][1] * Dnn[1]);
+        double nDn = 0.0;
+        for (int k = 0; k < 2; ++k)
+          for (int l = 0; l < 2; ++l) nDn += nn[k] * 0.5 * (De[k * 2 + l] + Dn[k * 2 + l]) * nn[l];
+        sg[iq] = nDn;
+      }
+      const double alpha = c_pen * std::max(area / m.vol[e], area / m.vol[n]);
+      for (int iq = 0; iq < q; ++iq) {
+        const double vals[5] = {a0[iq], a1[iq], b0[iq], b1[iq], wdS[iq] * alpha * sg[iq]};
+        for (int comp = 0; comp < 5; ++comp)
+          out.face[(((size_t)sl * nf + f) * q * 5 + iq * 5 + comp) * 32 + lane] = (float)vals[comp];
+      }
+    }
+  }
+  if (bad) { err = "matrix-free geometry: bad Jacobian or non-matching face points"; return AGG_EINVAL; }
+  return AGG_OK;
 }
 
 }  // namespace aggmg

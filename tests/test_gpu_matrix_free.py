@@ -1,0 +1,85 @@
+"""Matrix-free fine operator (float32, 2D) of the V-cycle against the oracle's
+assembled float64 operator, and the solver built on it against the float64
+oracle (the float32 V-cycle tolerance and the 1e-8 trajectory bound)."""
+import numpy as np
+import pytest
+
+from oracle import monodomain as omd
+from oracle import multigrid as omg
+from paper_2602_16312_gb300 import workloads as W
+
+from gpu_util import oracle_setup, rel, step_opts
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_16312_gb300 import build
+    build.build()
+
+
+def _dev(x):
+    return torch.tensor(np.asarray(x), dtype=torch.float64, device="cuda")
+
+
+CASES = {
+    "jsquare2d_q1_30": lambda: W.jittered_square_2d(n=30, degree=1, n_levels=3),
+    "jsquare2d_q2_30": lambda: W.jittered_square_2d(n=30, degree=2, n_levels=3),
+    "jsquare2d_q3_18": lambda: W.jittered_square_2d(n=18, degree=3, n_levels=2),
+    "square2d_q1_16": lambda: W.square_2d_fhn(16, 1),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_matrix_free_operator_matches_assembled(name):
+    from paper_2602_16312_gb300 import aggmg
+    wl = CASES[name]()
+    disc, ho = oracle_setup(wl)
+    hier = aggmg.Hierarchy(aggmg.Mesh.from_workload(wl), 1.0 / wl.dt, wl.maps, precision="f32", fine="mf")
+    x = np.random.default_rng(51).standard_normal(disc.n)
+    y = torch.empty(disc.n, dtype=torch.float64, device="cuda")
+    hier.operator_apply(-1, _dev(x), y)
+    torch.cuda.synchronize()
+    assert rel(y.cpu().numpy(), ho.levels[0].A @ x) <= 2e-6
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_matrix_free_vcycle_and_trajectory(name):
+    from paper_2602_16312_gb300 import aggmg
+    wl = CASES[name]()
+    disc, ho = oracle_setup(wl)
+    hier = aggmg.Hierarchy(aggmg.Mesh.from_workload(wl), 1.0 / wl.dt, wl.maps, precision="f32", fine="mf")
+    r = np.random.default_rng(52).standard_normal(disc.n)
+    z = torch.empty(disc.n, dtype=torch.float64, device="cuda")
+    hier.vcycle_apply(_dev(r), z)
+    torch.cuda.synchronize()
+    assert rel(z.cpu().numpy(), omg.vcycle(ho, r)) <= 5e-6
+    opts = step_opts(wl)
+    mask = wl.stim_mask_nodal()
+    sim = aggmg.Monodomain(hier, wl.dt, wl.ionic, iapp_mask=_dev(mask), iapp_value=wl.iapp_value,
+                           iapp_steps=wl.iapp_steps, rtol=wl.rtol, flexible=True)
+    u = torch.zeros(disc.n, dtype=torch.float64, device="cuda")
+    w = torch.zeros(disc.n, dtype=torch.float64, device="cuda")
+    uo, wo = np.zeros(disc.n), np.zeros(disc.n)
+    for n in range(5):
+        uo, wo, res = omd.step(disc, ho, opts, uo, wo, mask, n)
+        its = sim.step(u, w, 1)
+        assert rel(u.cpu().numpy(), uo) <= 1e-8, n
+        assert abs(its[0] - res.iterations) <= 3
+    sim.close()
+
+
+def test_matrix_free_rejected_where_unsupported():
+    from paper_2602_16312_gb300 import aggmg
+    wl = W.jittered_cube_3d(n=4, degree=1, n_levels=2, group=2)
+    with pytest.raises(aggmg.AggError) as e:
+        aggmg.Hierarchy(aggmg.Mesh.from_workload(wl), 1.0 / wl.dt, wl.maps, precision="f32", fine="mf")
+    assert e.value.status == aggmg.AGG_EUNSUPPORTED
+    wl = W.jittered_square_2d(n=8, degree=2, n_levels=2)
+    with pytest.raises(aggmg.AggError) as e:
+        aggmg.Hierarchy(aggmg.Mesh.from_workload(wl), 1.0 / wl.dt, wl.maps, precision="f64", fine="mf")
+    assert e.value.status == aggmg.AGG_EUNSUPPORTED
