@@ -28,6 +28,7 @@ METRIC = "time-steps/s and MDoF/s of MG-PCG at 1e-8 rel. residual; % of HBM peak
 UNIT = "time-steps/s"
 KERNEL_NAMES = {0: "k_spmv<double> (fine float64 SpMV, outer CG)",
                 1: "k_cheb (fine Chebyshev block-Jacobi step, V-cycle precision)"}
+KERNEL_NAMES_MF = {1: "k_cheb<MfOp> (fine Chebyshev block-Jacobi step, matrix-free float32 operator)"}
 
 
 def parse():
@@ -37,8 +38,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="f32", choices=["f32", "f64", "bf16s"])
-    ap.add_argument("--fine", default="bsr", choices=["bsr", "mf"],
-                    help="V-cycle level-0 operator: assembled blocks or matrix-free")
+    ap.add_argument("--fine", default=None, choices=["bsr", "mf"],
+                    help="V-cycle level-0 operator: assembled blocks or matrix-free "
+                         "(default: matrix-free for 2D float32 V-cycles, assembled otherwise)")
     ap.add_argument("--workload", default="jsquare2d", choices=list(WORKLOADS))
     ap.add_argument("--n", type=int, default=None, help="elements per direction (box workloads)")
     ap.add_argument("--e2e-steps", type=int, default=10)
@@ -192,6 +194,8 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
     dev = torch.device("cuda")
     wl = workload(args)
+    if args.fine is None:
+        args.fine = "mf" if (wl.mesh.dim == 2 and args.form != "f64" and wl.degree <= 3) else "bsr"
     t0 = time.time()
     mesh = aggmg.Mesh.from_workload(wl)
     hier = aggmg.Hierarchy(mesh, 1.0 / wl.dt, wl.maps, precision=args.form, fine=args.fine)
@@ -269,7 +273,7 @@ def run_ours(args, rank, world):
         roof = {"bound": "hbm", "achieved": kbytes / t_k / 1e9, "peak": hbm, "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
-    roof["kernel"] = KERNEL_NAMES[kid]
+    roof["kernel"] = KERNEL_NAMES_MF[kid] if args.fine == "mf" else KERNEL_NAMES[kid]
     roof["us_per_launch"] = t_k * 1e6
     roof["algorithmic_bytes"] = kbytes
     roof["peak_source"] = "MEASURED_PEAKS.json hbm_gbs (of measured)" if roof["bound"] == "hbm" else \
