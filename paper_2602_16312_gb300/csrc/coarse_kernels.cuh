@@ -1,0 +1,138 @@
+// Coarse-level kernels (levels >= 1, B <= 32): one thread per (unit, row).
+// Coarse levels have few units, so the one-thread-per-unit kernels of the
+// fine level leave most of the GPU idle and walk whole block rows
+// serially; here floor(32/B) units share a warp, lane r of a unit owns row
+// r, blocks are stored column-major per unit ([c*B + r]) so the lanes of a
+// unit read consecutive entries, and the rows of a unit's residual are
+// exchanged with warp shuffles for the block-inverse and P^T products.
+#pragma once
+#include "kernels.cuh"
+
+namespace aggmg {
+
+constexpr int RL_NT = 128;   // threads per block of the row-lane kernels
+
+template <typename T>
+struct CsrBlocks {           // block CSR with column-major blocks
+  const int32_t* rowptr;     // [n + 1]
+  const int32_t* cols;       // [nnzb]
+  const T* vals;             // [nnzb][B*B], entry (r, c) at c*B + r
+  int64_t n;
+};
+
+template <int B>
+struct RowLane {
+  static constexpr int UPW = 32 / B;          // units per warp
+  int64_t unit;
+  int r, base, lane;
+  bool active;
+  __device__ __forceinline__ RowLane(int64_t n) {
+    lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * RL_NT + threadIdx.x) >> 5;
+    const int sub = lane / B;
+    r = lane - sub * B;
+    base = sub * B;
+    unit = warp * UPW + sub;
+    active = (sub < UPW) && (unit < n);
+  }
+};
+
+// (A x)_r of the lane's unit
+template <typename T, int B>
+__device__ __forceinline__ T rl_row(const CsrBlocks<T>& A, const RowLane<B>& L, const T* __restrict__ x) {
+  T s = T(0);
+  if (!L.active) return s;
+  const int j0 = A.rowptr[L.unit], j1 = A.rowptr[L.unit + 1];
+  for (int j = j0; j < j1; ++j) {
+    const int col = A.cols[j];
+    const T* blk = A.vals + (size_t)j * B * B + L.r;
+    const T* xb = x + (size_t)col * B;
+#pragma unroll
+    for (int c = 0; c < B; ++c) s += blk[c * B] * xb[c];
+  }
+  return s;
+}
+
+// sum_c M[r][c] t_c with t distributed over the unit's lanes (column-major M)
+template <typename T, typename TD, int B>
+__device__ __forceinline__ T rl_block(const TD* __restrict__ M, const RowLane<B>& L, T t) {
+  T s = T(0);
+  const TD* m = M + (size_t)L.unit * B * B + L.r;
+#pragma unroll
+  for (int c = 0; c < B; ++c) {
+    const T tc = __shfl_sync(0xffffffffu, t, L.base + c);
+    if (L.active) s += (T)m[c * B] * tc;
+  }
+  return s;
+}
+
+// KIND 0/1/2 as k_cheb, one (unit, row) per thread
+template <typename T, typename TD, int B, int KIND>
+static __global__ void __launch_bounds__(RL_NT) k_rl_cheb(CsrBlocks<T> A, const TD* __restrict__ Dinv,
+                                                          const T* __restrict__ rhs, const T* __restrict__ x_old,
+                                                          T* __restrict__ x_new, T* __restrict__ d, T c1, T c2,
+                                                          const CGState* st) {
+  if (st && st->done) return;
+  const RowLane<B> L(A.n);
+  const size_t o = (size_t)L.unit * B + L.r;
+  T t = T(0);
+  if (L.active) t = (KIND == 0) ? rhs[o] : rhs[o] - rl_row<T, B>(A, L, x_old);
+  const T s = rl_block<T, TD, B>(Dinv, L, t);
+  if (!L.active) return;
+  const T dn = (KIND == 2) ? c1 * d[o] + c2 * s : c2 * s;
+  d[o] = dn;
+  x_new[o] = (KIND == 0) ? dn : x_old[o] + dn;
+}
+
+// S_u[j] = sum_i P_u[i][j] (rhs - A x)_u[i]   (P column-major: (i, j) at j*B + i)
+template <typename T, int B>
+static __global__ void __launch_bounds__(RL_NT) k_rl_resid_restrict(CsrBlocks<T> A, const T* __restrict__ P,
+                                                                    const T* __restrict__ rhs, const T* __restrict__ x,
+                                                                    T* __restrict__ S, const CGState* st) {
+  if (st && st->done) return;
+  const RowLane<B> L(A.n);
+  const size_t o = (size_t)L.unit * B + L.r;
+  T t = T(0);
+  if (L.active) t = rhs[o] - rl_row<T, B>(A, L, x);
+  // lane j (as column index) needs P[i][j] for all i: entries j*B + i, i.e. row j of P^T
+  T s = T(0);
+  const T* pj = P + (size_t)L.unit * B * B + (size_t)L.r * B;
+#pragma unroll
+  for (int i = 0; i < B; ++i) {
+    const T ti = __shfl_sync(0xffffffffu, t, L.base + i);
+    if (L.active) s += pj[i] * ti;
+  }
+  if (L.active) S[o] = s;
+}
+
+// x_u[r] += sum_j P_u[r][j] e_parent[j]
+template <typename T, int B>
+static __global__ void __launch_bounds__(RL_NT) k_rl_prolong(const T* __restrict__ P, const int32_t* __restrict__ parent,
+                                                             const T* __restrict__ ec, T* __restrict__ x, int64_t n,
+                                                             const CGState* st) {
+  if (st && st->done) return;
+  const RowLane<B> L(n);
+  if (!L.active) return;
+  const T* pr = P + (size_t)L.unit * B * B + L.r;
+  const T* eb = ec + (size_t)parent[L.unit] * B;
+  T s = T(0);
+#pragma unroll
+  for (int j = 0; j < B; ++j) s += pr[j * B] * eb[j];
+  x[(size_t)L.unit * B + L.r] += s;
+}
+
+// y = A x (levels >= 1, for agg_operator_apply)
+template <typename T, int B>
+static __global__ void __launch_bounds__(RL_NT) k_rl_spmv(CsrBlocks<T> A, const T* __restrict__ x, T* __restrict__ y) {
+  const RowLane<B> L(A.n);
+  const T s = rl_row<T, B>(A, L, x);
+  if (L.active) y[(size_t)L.unit * B + L.r] = s;
+}
+
+template <int B>
+inline int64_t rl_grid(int64_t n) {
+  const int64_t warps = (n + RowLane<B>::UPW - 1) / RowLane<B>::UPW;
+  return (warps * 32 + RL_NT - 1) / RL_NT;
+}
+
+}  // namespace aggmg

@@ -20,6 +20,7 @@
 #include "engine.h"
 #include "kernels.cuh"
 #include "mf_kernels.cuh"
+#include "coarse_kernels.cuh"
 
 namespace aggmg {
 
@@ -46,6 +47,7 @@ inline __nv_bfloat16 to_storage<__nv_bfloat16>(double v) {
 template <typename T, typename TD, int B>
 class Engine : public EngineBase {
   static constexpr int NTB = UnitThreads<B>::value;
+  static constexpr bool kRL = (B <= 32);
   // matrix-free fine operator: float32 V-cycle on 2D elements of p = 1..3
   static constexpr bool kMf = std::is_same<T, float>::value && (B == 4 || B == 9 || B == 16);
   using MfOpT = typename std::conditional<kMf, MfOp<kMf ? B : 9>, SellOp<T, B>>::type;
@@ -64,6 +66,10 @@ class Engine : public EngineBase {
     int64_t* perm = nullptr;
     T *xa = nullptr, *xb = nullptr, *d = nullptr, *rhs = nullptr, *S = nullptr;
     std::vector<T> c1, c2;
+    // row-lane copies for levels >= 1 (column-major blocks)
+    CsrBlocks<T> rl{};
+    TD* rl_dinv = nullptr;
+    T* rl_P = nullptr;
     SellView<T> A() const { return SellView<T>{slice_ptr, cols, vals, nsl}; }
   };
 
@@ -172,6 +178,17 @@ class Engine : public EngineBase {
     return s;
   }
 
+  // B x B row-major blocks -> column-major copies in storage type TS
+  template <typename TS>
+  int upload_colmajor(const double* blocks, int64_t nblk, TS** out, std::string& err) {
+    std::vector<TS> hv((size_t)nblk * B * B);
+    for (int64_t k = 0; k < nblk; ++k)
+      for (int r = 0; r < B; ++r)
+        for (int c = 0; c < B; ++c)
+          hv[(size_t)k * B * B + c * B + r] = to_storage<TS>(blocks[(size_t)k * B * B + r * B + c]);
+    return upload(out, hv.data(), hv.size(), err);
+  }
+
   template <typename TS>
   int upload_blocks(const std::vector<double>& blocks, int64_t n, int64_t nsl, TS** out, std::string& err) {
     constexpr int KP = Pad<TS, B>::KP;
@@ -195,7 +212,35 @@ class Engine : public EngineBase {
     if constexpr (kMf) {
       if (l == 0 && mf_) return vc_level(l, mfop_, s);
     }
+    if constexpr (kRL) {
+      if (l > 0) return vc_rowlane(l, s);
+    }
     return vc_level(l, SellOp<T, B>{v.A()}, s);
+  }
+
+  // One coarse level (l >= 1) with the row-lane kernels.
+  T* vc_rowlane(int l, cudaStream_t s) {
+    Lev& v = lev_[l];
+    T* xo = v.xa;
+    T* xn = v.xb;
+    const int64_t g = rl_grid<kRL ? B : 1>(v.n);
+    k_rl_cheb<T, TD, B, 0><<<g, RL_NT, 0, s>>>(v.rl, v.rl_dinv, v.rhs, nullptr, xo, v.d, T(0), v.c2[0], st_);
+    for (int k = 1; k < degree_; ++k) {
+      k_rl_cheb<T, TD, B, 2><<<g, RL_NT, 0, s>>>(v.rl, v.rl_dinv, v.rhs, xo, xn, v.d, v.c1[k], v.c2[k], st_);
+      std::swap(xo, xn);
+    }
+    Lev& c = lev_[l + 1];
+    k_rl_resid_restrict<T, B><<<g, RL_NT, 0, s>>>(v.rl, v.rl_P, v.rhs, xo, v.S, st_);
+    k_segsum<T, B><<<cdiv(c.n * B, 256), 256, 0, s>>>(c.child_ptr, v.S, c.rhs, c.n, st_);
+    T* ec = vc(l + 1, s);
+    k_rl_prolong<T, B><<<g, RL_NT, 0, s>>>(v.rl_P, v.parent, ec, xo, v.n, st_);
+    k_rl_cheb<T, TD, B, 1><<<g, RL_NT, 0, s>>>(v.rl, v.rl_dinv, v.rhs, xo, xn, v.d, T(0), v.c2[0], st_);
+    std::swap(xo, xn);
+    for (int k = 1; k < degree_; ++k) {
+      k_rl_cheb<T, TD, B, 2><<<g, RL_NT, 0, s>>>(v.rl, v.rl_dinv, v.rhs, xo, xn, v.d, v.c1[k], v.c2[k], st_);
+      std::swap(xo, xn);
+    }
+    return xo;
   }
 
   // One level of the V-cycle with the level operator `op` (assembled blocks
@@ -398,6 +443,17 @@ class Engine : public EngineBase {
         if ((rc = dalloc(&v.xb, v.nvec, err))) return rc;
         if ((rc = dalloc(&v.d, v.nvec, err))) return rc;
         if ((rc = dalloc(&v.S, v.nvec, err))) return rc;
+        if (kRL && l > 0) {
+          std::vector<int32_t> rp(hl.A.rowptr.begin(), hl.A.rowptr.end());
+          int32_t *drp, *dcol;
+          T* dval;
+          if ((rc = upload(&drp, rp.data(), rp.size(), err))) return rc;
+          if ((rc = upload(&dcol, hl.A.col.data(), hl.A.col.size(), err))) return rc;
+          if ((rc = upload_colmajor<T>(hl.A.val.data(), hl.A.nnzb(), &dval, err))) return rc;
+          v.rl = CsrBlocks<T>{drp, dcol, dval, hl.n};
+          if ((rc = upload_colmajor<TD>(hl.Dinv.data(), hl.n, &v.rl_dinv, err))) return rc;
+          if ((rc = upload_colmajor<T>(hl.P.data(), hl.n, &v.rl_P, err))) return rc;
+        }
       }
       if (l > 0) {
         if ((rc = upload(&v.child_ptr, hl.child_ptr.data(), hl.child_ptr.size(), err))) return rc;
