@@ -227,7 +227,9 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
   constexpr int NTB = UnitThreads<B>::value;
   constexpr int KP = Pad<double, B>::KP;
   const int lane = threadIdx.x & 31;
-  for (int64_t slice = first_slice<NTB>(); slice < nslices; slice += slice_stride<NTB>()) {
+  {
+  const int64_t slice = first_slice<NTB>();
+  if (slice >= nslices) return;
   const int64_t unit = slice * SL + lane;
   const size_t o = (size_t)unit * B;
   const double ia = (*step < iapp_steps) ? iapp_value : 0.0;
@@ -297,7 +299,9 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
   constexpr int NTB = UnitThreads<B>::value;
   constexpr int KP = Pad<double, B>::KP;
   const int lane = threadIdx.x & 31;
-  for (int64_t slice = first_slice<NTB>(); slice < nslices; slice += slice_stride<NTB>()) {
+  {
+  const int64_t slice = first_slice<NTB>();
+  if (slice >= nslices) return;
   const int64_t unit = slice * SL + lane;
   const size_t o = (size_t)unit * B;
   double q[B];
@@ -338,7 +342,9 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
   constexpr int NTB = UnitThreads<B>::value;
   constexpr int KP = Pad<double, B>::KP;
   const int lane = threadIdx.x & 31;
-  for (int64_t slice = first_slice<NTB>(); slice < A.nslices; slice += slice_stride<NTB>()) {
+  {
+  const int64_t slice = first_slice<NTB>();
+  if (slice >= A.nslices) return;
   const int64_t unit = slice * SL + lane;
   const size_t o = (size_t)unit * B;
   // sum_r l[r] (M1 x1 + M2 x2)[r] for two sliced blocks (M2 may be null)

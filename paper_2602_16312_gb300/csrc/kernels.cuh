@@ -164,16 +164,10 @@ __device__ __forceinline__ void block_mtv_out(const TS* base, int lane, const A*
   }
 }
 
-// Unit kernels loop over slices (one warp per slice at a time); the host
-// sizes the grid so that every warp gets the same number of slices and all
-// warps are resident at once (no partial last wave).
+// Unit kernels: one warp per slice of 32 units; the grid covers every slice.
 template <int NTB>
 __device__ __forceinline__ int64_t first_slice() {
   return (int64_t)blockIdx.x * (NTB / 32) + (threadIdx.x >> 5);
-}
-template <int NTB>
-__device__ __forceinline__ int64_t slice_stride() {
-  return (int64_t)gridDim.x * (NTB / 32);
 }
 
 template <typename T>
@@ -285,7 +279,8 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
   if (st && st->done) return;
   const int lane = threadIdx.x & 31;
   double part = 0.0;
-  for (int64_t slice = first_slice<NTB>(); slice < A.nslices; slice += slice_stride<NTB>()) {
+  const int64_t slice = first_slice<NTB>();
+  if (slice < A.nslices) {
     const int64_t unit = slice * SL + lane;
     T acc[B];
 #pragma unroll
@@ -328,7 +323,9 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
   if (st && st->done) return;
   constexpr int KPD = Pad<TD, B>::KP;
   const int lane = threadIdx.x & 31;
-  for (int64_t slice = first_slice<NTB>(); slice < nslices; slice += slice_stride<NTB>()) {
+  {
+  const int64_t slice = first_slice<NTB>();
+  if (slice >= nslices) return;
   const int64_t unit = slice * SL + lane;
   const size_t o = (size_t)unit * B;
   const TD* Db = Dinv + (size_t)slice * SL * KPD;
@@ -385,7 +382,9 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
   if (st && st->done) return;
   constexpr int KP = Pad<T, B>::KP;
   const int lane = threadIdx.x & 31;
-  for (int64_t slice = first_slice<NTB>(); slice < A.nslices(); slice += slice_stride<NTB>()) {
+  {
+  const int64_t slice = first_slice<NTB>();
+  if (slice >= A.nslices()) return;
   const int64_t unit = slice * SL + lane;
   const size_t o = (size_t)unit * B;
   const T* Pb = P + (size_t)slice * SL * KP;
@@ -400,7 +399,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
 #pragma unroll
     for (int r = 0; r < B; ++r) acc[r] = rhs[o + r] - acc[r];
     block_mtv_out<T, T, B>(Pb, lane, acc, S + o);
-    continue;
+    return;
   } else {
     T acc[B];
 #pragma unroll
@@ -439,7 +438,9 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
   if (st && st->done) return;
   constexpr int KP = Pad<T, B>::KP;
   const int lane = threadIdx.x & 31;
-  for (int64_t slice = first_slice<NTB>(); slice < nslices; slice += slice_stride<NTB>()) {
+  {
+  const int64_t slice = first_slice<NTB>();
+  if (slice >= nslices) return;
   const int64_t unit = slice * SL + lane;
   const size_t o = (size_t)unit * B;
   const T* eb = ec + (size_t)parent[unit] * B;

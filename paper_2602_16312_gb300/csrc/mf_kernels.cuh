@@ -220,7 +220,9 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value) k_op_apply(Op op
                                                                           T* __restrict__ y) {
   constexpr int NTB = UnitThreads<B>::value;
   const int lane = threadIdx.x & 31;
-  for (int64_t slice = first_slice<NTB>(); slice < op.nslices(); slice += slice_stride<NTB>()) {
+  {
+  const int64_t slice = first_slice<NTB>();
+  if (slice >= op.nslices()) return;
     T acc[B];
 #pragma unroll
     for (int r = 0; r < B; ++r) acc[r] = T(0);
