@@ -80,6 +80,45 @@ struct MfOp {
     float u[N * N];
 #pragma unroll
     for (int i = 0; i < N * N; ++i) u[i] = x[(size_t)unit * B + i];
+#ifndef AGG_MF_CELL_DIRECT
+#define AGG_MF_CELL_DIRECT 0
+#endif
+    const float* cd = V.cell + (size_t)slice * Q * Q * 4 * SL + lane;
+    if constexpr (AGG_MF_CELL_DIRECT) {
+      // ---- cell term point by point: more FP32 work, few live registers
+#pragma unroll 1
+      for (int l = 0; l < Q; ++l) {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+          float uq = 0.f, g0 = 0.f, g1 = 0.f;
+#pragma unroll
+          for (int b = 0; b < N; ++b) {
+            float su = 0.f, sd = 0.f;
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+              su += T.L[a][k] * u[a + N * b];
+              sd += T.D[a][k] * u[a + N * b];
+            }
+            uq += T.L[b][l] * su;
+            g0 += T.L[b][l] * sd;
+            g1 += T.D[b][l] * su;
+          }
+          const int iq = k + Q * l;
+          const float G00 = __ldg(cd + (iq * 4 + 0) * SL), G01 = __ldg(cd + (iq * 4 + 1) * SL);
+          const float G11 = __ldg(cd + (iq * 4 + 2) * SL), mm = __ldg(cd + (iq * 4 + 3) * SL);
+          const float w0 = G00 * g0 + G01 * g1;
+          const float w1 = G01 * g0 + G11 * g1;
+          const float wm = mm * uq;
+#pragma unroll
+          for (int b = 0; b < N; ++b) {
+            const float cb0 = T.L[b][l] * w0, cb1 = T.D[b][l] * w1 + T.L[b][l] * wm;
+#pragma unroll
+            for (int a = 0; a < N; ++a) acc[a + N * b] += T.D[a][k] * cb0 + T.L[a][k] * cb1;
+          }
+        }
+      }
+    } else {
+    // ---- cell term by sum factorisation (index i = a + N b, qp = k + Q l)
     // ---- cell term by sum factorisation (index i = a + N b, qp = k + Q l)
     float tu[N][Q], td[N][Q];
 #pragma unroll
@@ -100,7 +139,6 @@ struct MfOp {
     for (int b = 0; b < N; ++b)
 #pragma unroll
       for (int k = 0; k < Q; ++k) { p0[b][k] = 0.f; p1[b][k] = 0.f; }
-    const float* cd = V.cell + (size_t)slice * Q * Q * 4 * SL + lane;
 #pragma unroll
     for (int l = 0; l < Q; ++l)
 #pragma unroll
@@ -134,6 +172,7 @@ struct MfOp {
         for (int k = 0; k < Q; ++k) s += T.D[a][k] * p0[b][k] + T.L[a][k] * p1[b][k];
         acc[a + N * b] += s;
       }
+    }
     // ---- face terms
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
