@@ -9,10 +9,17 @@ Per step (Section 3.1, the three bullet points after Eq. fully_discrete):
      f_i = I_app,i(t_{n+1}) - chi I_ion(U*_i, w_i^{n+1})
   3. solve A0 u^{n+1} = b by MG-PCG warm-started from u^n.
 
-Scheme: IMEX backward Euler (the workloads' form of Eq. fully_discrete with
-the BDF2 history replaced by one level): mass coefficient c = chi C_m / dt of
-A0 = c M + A, U* = u^n, b = M (c u^n + f). The paper's BDF2 with the
-extrapolation U* = 2u^n - u^{n-1} is not part of this oracle.
+Schemes (mass coefficient c of A0 = c M + A):
+  scheme 0, IMEX backward Euler (the workloads' form): c = chi C_m / dt,
+      U* = u^n, w^{n+1} = w^n + dt H(u^n, w^n), b = M (c u^n + f).
+  scheme 1, BDF2 with extrapolation (Eq. fully_discrete): c = 3 chi C_m / (2 dt),
+      U* = 2u^n - u^{n-1}, W* = 2w^n - w^{n-1},
+      w^{n+1} = (4 w^n - w^{n-1})/3 + (2 dt / 3) H(U*, W*)   (explicit BDF2),
+      b = M (chi C_m (4 u^n - u^{n-1}) / (2 dt) + f), f with U* and w^{n+1}.
+      Start (reading: the paper only asks for "suitable initializations"):
+      u^{-1} = u^0 - dt u'(0), w^{-1} = w^0 - dt H(u^0, w^0), with u'(0) from
+      the semi-discrete system, chi C_m u' = I_app - chi I_ion - M^{-1} A u;
+      a first-order start would make the scheme first order.
 
 Adjoint (not in the paper): the discrete adjoint of this recurrence. With
 K = c M + A, a reverse step n+1 -> n takes ubar = dL/du^{n+1},
@@ -85,8 +92,11 @@ class StepOptions:
     cm: float = 1.0
     iapp_value: float = 1.0
     iapp_steps: int = 5
+    scheme: int = 0
 
     def mass_coeff(self):
+        if self.scheme == 1:
+            return 1.5 * self.chi * self.cm / self.dt
         return self.chi * self.cm / self.dt
 
 
@@ -105,7 +115,7 @@ def rhs(disc, opts: StepOptions, u, w_new, mask, n):
 
 
 def step(disc, hier, opts: StepOptions, u, w, mask, n):
-    """One time step n -> n+1. Returns (u_new, w_new, PCGResult)."""
+    """One backward-Euler time step n -> n+1. Returns (u_new, w_new, PCGResult)."""
     _, H = ionic(opts.ionic, u, w)
     w_new = w + opts.dt * H
     b = rhs(disc, opts, u, w_new, mask, n)
@@ -114,10 +124,42 @@ def step(disc, hier, opts: StepOptions, u, w, mask, n):
     return res.x, w_new, res
 
 
+def bdf2_start(disc, opts: StepOptions, u0, w0, mask):
+    """History (u^{-1}, w^{-1}) of the BDF2 scheme from the state at t = 0."""
+    import scipy.sparse.linalg as spl
+    chi, cm, dt = opts.chi, opts.cm, opts.dt
+    I, H = ionic(opts.ionic, u0, w0)
+    f0 = iapp(opts, mask, 0) - chi * I
+    MinvAu = spl.spsolve(disc.M.tocsc(), disc.A @ u0)
+    udot = (f0 - MinvAu) / (chi * cm)
+    return u0 - dt * udot, w0 - dt * H
+
+
+def bdf2_step(disc, hier, opts: StepOptions, u, u_prev, w, w_prev, mask, n):
+    """One BDF2 step n -> n+1 (scheme 1). Returns (u_new, w_new, PCGResult)."""
+    chi, cm, dt = opts.chi, opts.cm, opts.dt
+    ustar = 2.0 * u - u_prev
+    wstar = 2.0 * w - w_prev
+    _, H = ionic(opts.ionic, ustar, wstar)
+    w_new = (4.0 * w - w_prev) / 3.0 + (2.0 * dt / 3.0) * H
+    I, _ = ionic(opts.ionic, ustar, w_new)
+    f = iapp(opts, mask, n) - chi * I
+    b = disc.M @ (chi * cm / (2.0 * dt) * (4.0 * u - u_prev) + f)
+    res = pcg(hier.levels[0].A, b, u, lambda r: vcycle(hier, r), opts.rtol, opts.max_it)
+    return res.x, w_new, res
+
+
 def run(disc, hier, opts: StepOptions, u0, w0, mask, n_steps):
     """n_steps time steps from (u0, w0); returns (u, w, iterations list)."""
     u, w = u0.copy(), w0.copy()
     its = []
+    if opts.scheme == 1:
+        u_prev, w_prev = bdf2_start(disc, opts, u0, w0, mask)
+        for n in range(n_steps):
+            u_new, w_new, res = bdf2_step(disc, hier, opts, u, u_prev, w, w_prev, mask, n)
+            u_prev, w_prev, u, w = u, w, u_new, w_new
+            its.append(res.iterations)
+        return u, w, its
     for n in range(n_steps):
         u, w, res = step(disc, hier, opts, u, w, mask, n)
         its.append(res.iterations)
