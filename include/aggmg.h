@@ -214,19 +214,28 @@ agg_status agg_ionic_update(const agg_ionic_params* prm, double dt, int64_t n, c
 
 /* ------------------------------------------------------------------ time stepping */
 typedef struct {
-  double dt, chi_m, c_m;          /* mass coefficient must equal chi_m c_m / dt  */
+  double dt, chi_m, c_m;          /* mass coefficient: chi_m c_m / dt (scheme 0),
+                                     3 chi_m c_m / (2 dt) (scheme 1)             */
   agg_ionic_params ionic;
   const double* iapp_mask_dev;    /* [n_dofs] nodal stimulus mask (copied)        */
   double iapp_value;              /* I_app = iapp_value * mask for the first      */
   int iapp_steps;                 /* iapp_steps steps, zero afterwards            */
   agg_pcg_opts pcg;
+  int scheme;                     /* 0 IMEX backward Euler, 1 BDF2 (see below)    */
 } agg_sim_opts;
 
-/* One step n -> n+1 (Section 3.1 with the backward-Euler form of
- * Eq. fully_discrete and ionic current interpolation):
+/* One step n -> n+1 (Section 3.1, ionic current interpolation).
+ * scheme 0, backward-Euler form of Eq. fully_discrete:
  *   w^{n+1} = w^n + dt H(u^n, w^n)
  *   b = M (c u^n + I_app(t_{n+1}) - chi_m I_ion(u^n, w^{n+1})),  c = chi_m c_m/dt
- *   A0 u^{n+1} = b by PCG warm-started from u^n. */
+ * scheme 1, BDF2 with the extrapolation U* = 2u^n - u^{n-1} (Eq. fully_discrete):
+ *   W* = 2w^n - w^{n-1}, w^{n+1} = (4w^n - w^{n-1})/3 + (2dt/3) H(U*, W*)
+ *   b = M (chi_m c_m (4u^n - u^{n-1})/(2dt) + I_app(t_{n+1}) - chi_m I_ion(U*, w^{n+1}))
+ *   the history (u^{n-1}, w^{n-1}) is kept by the handle; at the first step
+ *   (and after agg_monodomain_set_clock) it is started at second order:
+ *   u^{-1} = u - dt u', chi_m c_m u' = I_app - chi_m I_ion(u, w) - M^{-1} A u,
+ *   w^{-1} = w - dt H(u, w).
+ * Both: A0 u^{n+1} = b by PCG warm-started from u^n. */
 agg_status agg_monodomain_create(agg_hier_t hier, const agg_sim_opts* opts, agg_sim_t* out);
 /* Advances n_steps steps in place on u_dev, w_dev ([n_dofs] each); the
  * stimulus clock is the handle's step counter (starts at 0). iters_out: host

@@ -58,7 +58,7 @@ class IonicParams(C.Structure):
 class SimOpts(C.Structure):
     _fields_ = [("dt", C.c_double), ("chi_m", C.c_double), ("c_m", C.c_double), ("ionic", IonicParams),
                 ("iapp_mask_dev", C.c_void_p), ("iapp_value", C.c_double), ("iapp_steps", C.c_int),
-                ("pcg", PCGOpts)]
+                ("pcg", PCGOpts), ("scheme", C.c_int)]
 
 
 _lib = None
@@ -373,10 +373,10 @@ class Monodomain:
     """agg_monodomain_create / agg_monodomain_step on a hierarchy."""
 
     def __init__(self, hier: Hierarchy, dt, ionic: dict, iapp_mask=None, iapp_value=1.0, iapp_steps=5,
-                 rtol=1e-8, atol=0.0, max_it=500, flexible=False, chi_m=1.0, c_m=1.0):
+                 rtol=1e-8, atol=0.0, max_it=500, flexible=False, chi_m=1.0, c_m=1.0, scheme=0):
         self._mask = iapp_mask
         o = SimOpts(dt, chi_m, c_m, ionic_params(ionic), C.c_void_p(_dptr(iapp_mask)) if iapp_mask is not None
-                    else None, iapp_value, iapp_steps, PCGOpts(rtol, atol, max_it, int(flexible)))
+                    else None, iapp_value, iapp_steps, PCGOpts(rtol, atol, max_it, int(flexible)), int(scheme))
         h = C.c_void_p()
         _check(lib().agg_monodomain_create(hier.handle, C.byref(o), C.byref(h)))
         self.handle = h

@@ -409,9 +409,11 @@ agg_status agg_monodomain_create(agg_hier_t h, const agg_sim_opts* o, agg_sim_t*
   if (s) return s;
   if ((s = check_device(h))) return s;
   if (!(o->dt > 0) || !(o->chi_m > 0) || !(o->c_m > 0)) return fail(AGG_EINVAL, "dt, chi_m, c_m must be > 0");
-  const double c = o->chi_m * o->c_m / o->dt;
+  if (o->scheme != 0 && o->scheme != 1) return fail(AGG_EINVAL, "scheme must be 0 or 1");
+  const double c = (o->scheme == 1 ? 1.5 : 1.0) * o->chi_m * o->c_m / o->dt;
   if (std::fabs(c - h->mass_coeff) > 1e-12 * std::fabs(c))
-    return fail(AGG_EINVAL, "hierarchy mass_coeff differs from chi_m c_m / dt");
+    return fail(AGG_EINVAL, o->scheme == 1 ? "hierarchy mass_coeff differs from 3 chi_m c_m / (2 dt)"
+                                           : "hierarchy mass_coeff differs from chi_m c_m / dt");
   if (o->ionic.model != AGG_FHN && o->ionic.model != AGG_ALIEV_PANFILOV) return fail(AGG_EINVAL, "ionic model");
   SimParams sp;
   sp.model = o->ionic.model;
@@ -426,6 +428,7 @@ agg_status agg_monodomain_create(agg_hier_t h, const agg_sim_opts* o, agg_sim_t*
   sp.cm = o->c_m;
   sp.iapp_value = o->iapp_mask_dev ? o->iapp_value : 0.0;
   sp.iapp_steps = o->iapp_steps;
+  sp.scheme = o->scheme;
   sp.pcg.rtol = o->pcg.rtol;
   sp.pcg.atol = o->pcg.atol;
   sp.pcg.max_it = o->pcg.max_it;
@@ -485,6 +488,7 @@ agg_status agg_monodomain_adjoint_step(agg_sim_t sim, const double* u_n, const d
 agg_status agg_monodomain_set_clock(agg_sim_t sim, int64_t step) {
   if (!sim || step < 0) return fail(AGG_EINVAL, "bad argument");
   sim->clock = step;
+  sim->h->eng->sim_invalidate_history();
   return AGG_OK;
 }
 

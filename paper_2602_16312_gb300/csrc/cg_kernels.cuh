@@ -264,6 +264,86 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
   }
 }
 
+// BDF2 history at the start (second-order derivative start), per element:
+//   u^{-1} = u - dt u',  chi C_m u' = I_app - chi I(u, w) - M^{-1} A u,
+//   w^{-1} = w - dt H(u, w),   with M^{-1} A u = M_e^{-1} (A0 u)_e - c u.
+template <int B>
+static __global__ void __launch_bounds__(UnitThreads<B>::value)
+    k_bdf2_start(const double* __restrict__ Minv, const double* __restrict__ A0u, const double* __restrict__ u,
+                 const double* __restrict__ w, const double* __restrict__ mask, double* __restrict__ up,
+                 double* __restrict__ wp, IonicParams prm, double dt, double chi, double cm, double c, double ia,
+                 int64_t nslices) {
+  constexpr int NTB = UnitThreads<B>::value;
+  constexpr int KP = Pad<double, B>::KP;
+  const int lane = threadIdx.x & 31;
+  const int64_t slice = first_slice<NTB>();
+  if (slice >= nslices) return;
+  const size_t o = (size_t)(slice * SL + lane) * B;
+  double t[B];
+#pragma unroll
+  for (int r = 0; r < B; ++r) t[r] = 0.0;
+  block_mv<double, double, B>(Minv + (size_t)slice * SL * KP, lane, A0u + o, t);
+#pragma unroll
+  for (int r = 0; r < B; ++r) {
+    const double ur = u[o + r], wr = w[o + r];
+    double I, H;
+    ionic_eval(prm, ur, wr, I, H);
+    const double f0 = ia * mask[o + r] - chi * I;
+    const double udot = (f0 - (t[r] - c * ur)) / (chi * cm);
+    up[o + r] = ur - dt * udot;
+    wp[o + r] = wr - dt * H;
+  }
+}
+
+// BDF2 step prologue (Eq. fully_discrete with extrapolation), per element:
+//   U* = 2u - up, W* = 2w - wp, w_new = (4w - wp)/3 + (2dt/3) H(U*, W*),
+//   f = I_app mask - chi I(U*, w_new), b_e = M_e (chi C_m (4u - up)/(2dt) + f);
+//   then the history shifts: up <- u, wp <- w, w <- w_new.
+template <int B>
+static __global__ void __launch_bounds__(UnitThreads<B>::value)
+    k_ionic_rhs_bdf2(const double* __restrict__ Me, const double* __restrict__ u, double* __restrict__ up,
+                     double* __restrict__ w, double* __restrict__ wp, const double* __restrict__ mask,
+                     double* __restrict__ b, IonicParams prm, double dt, double chi, double cm, double iapp_value,
+                     int64_t iapp_steps, const int64_t* __restrict__ step, int64_t nslices) {
+  constexpr int NTB = UnitThreads<B>::value;
+  constexpr int KP = Pad<double, B>::KP;
+  const int lane = threadIdx.x & 31;
+  const int64_t slice = first_slice<NTB>();
+  if (slice >= nslices) return;
+  const size_t o = (size_t)(slice * SL + lane) * B;
+  const double ia = (*step < iapp_steps) ? iapp_value : 0.0;
+  auto nodal = [&](int r) {
+    const double un = u[o + r], upr = up[o + r], wn = w[o + r], wpr = wp[o + r];
+    const double us = 2.0 * un - upr, ws = 2.0 * wn - wpr;
+    double I, H;
+    ionic_eval(prm, us, ws, I, H);
+    const double w1 = (4.0 * wn - wpr) / 3.0 + (2.0 * dt / 3.0) * H;
+    ionic_eval(prm, us, w1, I, H);
+    up[o + r] = un;
+    wp[o + r] = wn;
+    w[o + r] = w1;
+    return chi * cm / (2.0 * dt) * (4.0 * un - upr) + ia * mask[o + r] - chi * I;
+  };
+  double acc[B];
+#pragma unroll
+  for (int r = 0; r < B; ++r) acc[r] = 0.0;
+  const double* Mb = Me + (size_t)slice * SL * KP;
+  if constexpr (B > 32) {
+    __shared__ double tsh[B * NTB];
+    double* ts = tsh + threadIdx.x;
+#pragma unroll
+    for (int r = 0; r < B; ++r) ts[r * NTB] = nodal(r);
+    block_mv<double, double, B, NTB>(Mb, lane, ts, acc);
+  } else {
+    double tv[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) tv[r] = nodal(r);
+    block_mv<double, double, B>(Mb, lane, tv, acc);
+  }
+#pragma unroll
+  for (int r = 0; r < B; ++r) b[o + r] = acc[r];
+}
+
 // Partial derivatives of the ionic model at one DoF (I_u, I_w, H_u, H_w).
 __device__ __forceinline__ void ionic_jac(const IonicParams& p, double u, double w, double& Iu, double& Iw,
                                           double& Hu, double& Hw) {

@@ -26,6 +26,7 @@ struct SimParams {
   double dt = 0, chi = 1, cm = 1;
   double iapp_value = 0;
   int64_t iapp_steps = 0;
+  int scheme = 0;              // 0 IMEX backward Euler, 1 BDF2 with extrapolation
   SolveOpts pcg;
 };
 
@@ -44,6 +45,7 @@ class EngineBase {
   virtual int sim_step(int n_steps, double* u_user, double* w_user, int* iters_host, int64_t& clock,
                        cudaStream_t s, std::string& err) = 0;
   virtual int sim_destroy() = 0;
+  virtual void sim_invalidate_history() = 0;
   // one reverse time step (discrete adjoint), vectors in the caller's order
   virtual int adjoint_step(const double* u_n, const double* w_n, const double* u_np1, double* ubar, double* wbar,
                            double* grad, SolveResult& res, cudaStream_t s, std::string& err) = 0;

@@ -109,6 +109,10 @@ class Engine : public EngineBase {
   int cap_ = 1024;
   // adjoint data and buffers
   double *Ke_ = nullptr, *Y_ = nullptr;
+  // BDF2 history and inverse element mass blocks
+  double *up_ = nullptr, *wp_ = nullptr, *Minv_ = nullptr;
+  bool hist_valid_ = false;
+  std::vector<double> me_int_;     // element mass blocks, internal order (for M^-1)
   double *ua_ = nullptr, *wa_ = nullptr, *ub_ = nullptr, *wb_ = nullptr;
   cudaGraphExec_t step_exec_ = nullptr, step_pro_exec_ = nullptr, step_epi_exec_ = nullptr;
 
@@ -306,6 +310,12 @@ class Engine : public EngineBase {
 
   void launch_step_prologue(cudaStream_t s) {
     IonicParams ip{sp_.model, sp_.k, sp_.a, sp_.eps, sp_.gamma, sp_.mu1, sp_.mu2};
+    if (sp_.scheme == 1) {
+      k_ionic_rhs_bdf2<B><<<bgrid(0, lev_[0].nsl), NTB, 0, s>>>(Me_, x_, up_, w_, wp_, mask_, b_, ip, sp_.dt, sp_.chi,
+                                                              sp_.cm, sp_.iapp_value, sp_.iapp_steps, step_,
+                                                              lev_[0].nsl);
+      return;
+    }
     const double c = sp_.chi * sp_.cm / sp_.dt;
     k_ionic_rhs<B><<<bgrid(k_ionic_rhs<B>, lev_[0].nsl), NTB, 0, s>>>(Me_, x_, w_, mask_, b_, ip, sp_.dt, sp_.chi, c, sp_.iapp_value,
                                        sp_.iapp_steps, step_, lev_[0].nsl);
@@ -476,6 +486,7 @@ class Engine : public EngineBase {
       for (int64_t r = 0; r < m.ne; ++r)
         std::memcpy(&me[(size_t)r * B * B], &m.Me[(size_t)h.lev[0].perm[r] * B * B], sizeof(double) * B * B);
       if ((rc = upload_blocks<double>(me, m.ne, lev_[0].nsl, &Me_, err))) return rc;
+      me_int_.swap(me);
     }
     // adjoint data: volume forms and per-slot face parts in the fine operator's slot order
     if (m.adjoint_data) {
@@ -690,6 +701,14 @@ class Engine : public EngineBase {
       if ((rc = dalloc(&sim_status_, 1, err))) return rc;
     }
     const Lev& v0 = lev_[0];
+    if (p.scheme == 1 && !up_) {
+      if ((rc = dalloc(&up_, N, err))) return rc;
+      if ((rc = dalloc(&wp_, N, err))) return rc;
+      std::vector<double> minv(me_int_.size());
+      if (!spd_inverse_blocks(me_int_.data(), v0.n, B, minv.data())) { err = "element mass block not SPD"; return AGG_ENOTSPD; }
+      if ((rc = upload_blocks<double>(minv, v0.n, v0.nsl, &Minv_, err))) return rc;
+    }
+    hist_valid_ = false;
     if (mask_user)
       k_gather_units<double, double><<<cdiv(v0.n * B, 256), 256, 0, s>>>(mask_user, mask_, v0.perm, v0.n, B);
     AGG_CK(cudaMemsetAsync(step_, 0, sizeof(int64_t), s));
@@ -721,6 +740,16 @@ class Engine : public EngineBase {
     k_gather_units<double, double><<<g, 256, 0, s>>>(w_user, w_, v0.perm, v0.n, B);
     AGG_CK(cudaMemcpyAsync(step_, &clock, sizeof(int64_t), cudaMemcpyHostToDevice, s));
     AGG_CK(cudaMemsetAsync(sim_status_, 0, sizeof(int), s));
+    if (sp_.scheme == 1 && !hist_valid_) {
+      // second-order start of the BDF2 history from the current state
+      IonicParams ip{sp_.model, sp_.k, sp_.a, sp_.eps, sp_.gamma, sp_.mu1, sp_.mu2};
+      const double c = 1.5 * sp_.chi * sp_.cm / sp_.dt;
+      const double ia = (clock < sp_.iapp_steps) ? sp_.iapp_value : 0.0;
+      k_spmv<double, B, 0><<<bgrid(0, v0.nsl), NTB, 0, s>>>(A0_, x_, nullptr, q_, nullptr, nullptr);
+      k_bdf2_start<B><<<bgrid(0, v0.nsl), NTB, 0, s>>>(Minv_, q_, x_, w_, mask_, up_, wp_, ip, sp_.dt, sp_.chi, sp_.cm,
+                                                       c, ia, v0.nsl);
+      hist_valid_ = true;
+    }
     k_set_opts<<<1, 1, 0, s>>>(st_, sp_.pcg.rtol, sp_.pcg.atol, sp_.pcg.max_it, sp_.pcg.flexible);
     int done = 0;
     int status = 0;
@@ -805,6 +834,7 @@ class Engine : public EngineBase {
                    double* grad, SolveResult& res, cudaStream_t s, std::string& err) override {
     if (!sim_) { err = "no simulation"; return AGG_EINVAL; }
     if (!Ke_ || !Y_) { err = "the mesh was created without adjoint data (agg_mesh_desc.adjoint_data)"; return AGG_EINVAL; }
+    if (sp_.scheme != 0) { err = "the adjoint step is built for the backward-Euler scheme"; return AGG_EUNSUPPORTED; }
     int rc;
     const int64_t N = N0();
     if (!ua_) {
@@ -837,6 +867,8 @@ class Engine : public EngineBase {
     res.status = st_host_->status;
     return AGG_OK;
   }
+
+  void sim_invalidate_history() override { hist_valid_ = false; }
 
   int sim_destroy() override {
     sim_ = false;

@@ -115,6 +115,9 @@ struct MatrixFreeData {
 int matrix_free_build(const Mesh& m, const std::vector<int64_t>& perm, const std::vector<int64_t>& inv, double c,
                       MatrixFreeData& out, std::string& err);
 
+// inverses of n SPD B x B row-major blocks (Cholesky); false if one is not SPD
+bool spd_inverse_blocks(const double* blocks, int64_t n, int B, double* out);
+
 // y = A x on the host (block CSR, float64)
 void bsr_apply(const BlockCSR& A, const double* x, double* y);
 

@@ -118,6 +118,24 @@ double dot(const std::vector<double>& a, const std::vector<double>& b) {
 
 }  // namespace
 
+bool spd_inverse_blocks(const double* blocks, int64_t n, int B, double* out) {
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(+ : bad)
+  for (int64_t u = 0; u < n; ++u) {
+    std::vector<double> Lc(blocks + (size_t)u * B * B, blocks + (size_t)(u + 1) * B * B), Li((size_t)B * B);
+    if (!cholesky(Lc.data(), B)) { bad += 1; continue; }
+    lower_inverse(Lc.data(), Li.data(), B);
+    double* Di = out + (size_t)u * B * B;
+    for (int i = 0; i < B; ++i)
+      for (int j = 0; j < B; ++j) {
+        double sacc = 0.0;
+        for (int k = std::max(i, j); k < B; ++k) sacc += Li[k * B + i] * Li[k * B + j];
+        Di[i * B + j] = sacc;
+      }
+  }
+  return bad == 0;
+}
+
 int hierarchy_build(const Mesh& m, double c, const HierOptions& o, HostHierarchy& h, std::string& err) {
   const int L = o.L, B = m.B, dim = m.dim, p = m.p;
   if (L < 1) { err = "n_levels must be >= 1"; return AGG_EINVAL; }

@@ -130,3 +130,31 @@ def test_error_statuses():
     # zero right-hand side and zero guess: converged before the first iteration
     res = hier.pcg_solve(_dev(np.zeros(disc.n)), _dev(np.zeros(disc.n)))
     assert res["iterations"] == 0 and res["status"] == 0
+
+
+@pytest.mark.parametrize("name", ["square2d_q1_16", "jsquare2d_q2_30", "jcube3d_q2_6"])
+def test_bdf2_trajectory_matches_oracle(name):
+    """Scheme 1 (BDF2 with extrapolation and the derivative start) against the
+    oracle's BDF2: same iteration counts, states within 1e-10."""
+    aggmg = _aggmg()
+    wl = CASES[name]()
+    c = 1.5 / wl.dt
+    disc, ho = oracle_setup(wl, c=c)
+    opts = step_opts(wl)
+    opts.scheme = 1
+    mask = wl.stim_mask_nodal()
+    n_steps = 8
+    u_ref, w_ref, its_ref = omd.run(disc, ho, opts, np.zeros(disc.n), np.zeros(disc.n), mask, n_steps)
+    hier = aggmg.Hierarchy(aggmg.Mesh.from_workload(wl), c, wl.maps, precision="f64")
+    sim = aggmg.Monodomain(hier, wl.dt, wl.ionic, iapp_mask=_dev(mask), iapp_value=wl.iapp_value,
+                           iapp_steps=wl.iapp_steps, rtol=wl.rtol, scheme=1)
+    u = torch.zeros(disc.n, dtype=torch.float64, device="cuda")
+    w = torch.zeros(disc.n, dtype=torch.float64, device="cuda")
+    its = sim.step(u, w, 3) + sim.step(u, w, n_steps - 3)     # history carried across calls
+    sim.close()
+    assert its == its_ref
+    assert rel(u.cpu().numpy(), u_ref) <= 1e-10
+    assert rel(w.cpu().numpy(), w_ref) <= 1e-10
+    # the mass coefficient must match the scheme
+    with pytest.raises(aggmg.AggError):
+        aggmg.Monodomain(hier, wl.dt, wl.ionic, scheme=0)
