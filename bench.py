@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--form", default="f32", choices=["f32", "f64", "bf16s"])
     ap.add_argument("--fine", default=None, choices=["bsr", "mf"],
                     help="V-cycle level-0 operator: assembled blocks or matrix-free "
-                         "(default: matrix-free for 2D float32 V-cycles, assembled otherwise)")
+                         "(default: matrix-free for float32 V-cycles on quadrilaterals of p <= 3 "
+                         "and hexahedra of p <= 2, assembled otherwise)")
     ap.add_argument("--workload", default="jsquare2d", choices=list(WORKLOADS))
     ap.add_argument("--n", type=int, default=None, help="elements per direction (box workloads)")
     ap.add_argument("--e2e-steps", type=int, default=10)
@@ -195,7 +196,8 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda")
     wl = workload(args)
     if args.fine is None:
-        args.fine = "mf" if (wl.mesh.dim == 2 and args.form != "f64" and wl.degree <= 3) else "bsr"
+        mf_ok = wl.degree <= (3 if wl.mesh.dim == 2 else 2)
+        args.fine = "mf" if (args.form != "f64" and mf_ok) else "bsr"
     t0 = time.time()
     mesh = aggmg.Mesh.from_workload(wl)
     hier = aggmg.Hierarchy(mesh, 1.0 / wl.dt, wl.maps, precision=args.form, fine=args.fine)

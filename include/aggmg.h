@@ -116,9 +116,13 @@ typedef struct {
                                     blocks; 1 matrix-free (the SIPG form and
                                     mass term evaluated from quadrature data
                                     with sum factorisation, Section 5.2); 1
-                                    needs a 2D mesh with p <= 3, quad_extra 1
-                                    and a float32 V-cycle. The outer CG always
-                                    uses the assembled float64 operator.     */
+                                    needs quadrilaterals with p <= 3 or
+                                    hexahedra with p <= 2 whose neighbours
+                                    list each shared face's corners in the
+                                    same order, quad_extra 1 and a float32
+                                    V-cycle, else AGG_EUNSUPPORTED. The outer
+                                    CG always uses the assembled float64
+                                    operator.                                */
 } agg_mg_opts;
 
 void agg_mg_opts_default(agg_mg_opts* opts);

@@ -48,9 +48,11 @@ template <typename T, typename TD, int B>
 class Engine : public EngineBase {
   static constexpr int NTB = UnitThreads<B>::value;
   static constexpr bool kRL = (B <= 32);
-  // matrix-free fine operator: float32 V-cycle on 2D elements of p = 1..3
-  static constexpr bool kMf = std::is_same<T, float>::value && (B == 4 || B == 9 || B == 16);
-  using MfOpT = typename std::conditional<kMf, MfOp<kMf ? B : 9>, SellOp<T, B>>::type;
+  // matrix-free fine operator: float32 V-cycle on quadrilaterals of p = 1..3
+  // and hexahedra of p = 1, 2
+  static constexpr bool kMf =
+      std::is_same<T, float>::value && (B == 4 || B == 9 || B == 16 || B == 8 || B == 27);
+  using MfOpT = typename std::conditional<kMf, typename MfOpFor<kMf ? B : 9>::type, SellOp<T, B>>::type;
   bool mf_ = false;
   MfOpT mfop_{};
   int64_t mf_bytes_ = 0;
@@ -519,12 +521,12 @@ class Engine : public EngineBase {
       }
       if ((rc = upload(&Y_, hy.data(), hy.size(), err))) return rc;
     }
-    // matrix-free fine operator for the float32 V-cycle (2D)
+    // matrix-free fine operator for the float32 V-cycle
     if (fine_operator == 1) {
       if constexpr (kMf) {
         MatrixFreeData md;
         if ((rc = matrix_free_build(m, h.lev[0].perm, h.lev[0].inv, h.mass_coeff, md, err))) return rc;
-        if (md.q != MfDegree<kMf ? B : 9>::value + 2) { err = "matrix-free operator needs quad_extra = 1"; return AGG_EUNSUPPORTED; }
+        if (md.q != MfOpT::kDegree + 2) { err = "matrix-free operator needs quad_extra = 1"; return AGG_EUNSUPPORTED; }
         float *cell, *face;
         int32_t* nbr;
         int8_t* code;
@@ -551,7 +553,7 @@ class Engine : public EngineBase {
         mf_bytes_ = (int64_t)(md.cell.size() * 4 + md.face.size() * 4 + md.nbr.size() * 4 + md.code.size());
         mf_ = true;
       } else {
-        err = "the matrix-free fine operator needs a 2D mesh (p <= 3) and a float32 V-cycle";
+        err = "the matrix-free fine operator needs quadrilaterals of p <= 3 or hexahedra of p <= 2 and a float32 V-cycle";
         return AGG_EUNSUPPORTED;
       }
     }

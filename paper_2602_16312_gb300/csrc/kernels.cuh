@@ -15,6 +15,7 @@
 // returns at once when the iteration has converged, so extra launches after
 // convergence do no work.
 #pragma once
+#include <type_traits>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -90,6 +91,15 @@ template <> struct ChunkLoad<__nv_bfloat16, float> {
 // per-thread vectors are staged in shared memory.
 template <int B> struct UnitThreads {
   static constexpr int value = (B > 32) ? 64 : 128;
+};
+
+// Minimum resident blocks per SM asked of the compiler for the kernels that
+// evaluate an operator Op: Op::kMinBlocks where Op has it, else 1.
+template <typename Op, typename = void> struct OpMinBlocks {
+  static constexpr int value = 1;
+};
+template <typename Op> struct OpMinBlocks<Op, std::void_t<decltype(Op::kMinBlocks)>> {
+  static constexpr int value = Op::kMinBlocks;
 };
 
 // acc[r] += sum_c M[r][c] x[c*XS] for one sliced block M (storage TS, math
@@ -316,7 +326,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
 // Blocks of more than 32 DoFs keep the residual in the thread's own strided
 // shared-memory slot (read by that thread only) instead of registers.
 template <typename T, typename TD, int B, int KIND, typename Op>
-static __global__ void __launch_bounds__(UnitThreads<B>::value)
+static __global__ void __launch_bounds__(UnitThreads<B>::value, OpMinBlocks<Op>::value)
     k_cheb(Op A, const TD* __restrict__ Dinv, const T* __restrict__ rhs, const T* __restrict__ x_old,
            T* __restrict__ x_new, T* __restrict__ d, T c1, T c2, int64_t nslices, const CGState* st) {
   constexpr int NTB = UnitThreads<B>::value;
@@ -375,7 +385,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
 // ---------------------------------------------------------------- transfers
 // S_u = P_u^T (rhs_u - (A x)_u): residual of the pre-smoothed iterate, restricted
 template <typename T, int B, typename Op>
-static __global__ void __launch_bounds__(UnitThreads<B>::value)
+static __global__ void __launch_bounds__(UnitThreads<B>::value, OpMinBlocks<Op>::value)
     k_resid_restrict(Op A, const T* __restrict__ P, const T* __restrict__ rhs, const T* __restrict__ x,
                      T* __restrict__ S, const CGState* st) {
   constexpr int NTB = UnitThreads<B>::value;

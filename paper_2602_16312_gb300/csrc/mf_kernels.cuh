@@ -1,4 +1,4 @@
-// Matrix-free fine-level operator (2D quadrilaterals, float32): the SIPG
+// Matrix-free fine-level operator (quadrilaterals, hexahedra; float32): the SIPG
 // form plus mass term y = (c M + A) x evaluated element by element from
 // per-quadrature-point geometry (Section 5.2: operator evaluation by
 // quadrature with sum factorisation for tensor-product bases), instead of
@@ -69,6 +69,7 @@ __device__ __forceinline__ void mf_nbr_face(const MfTables& T, const float* xn, 
 
 template <int B>
 struct MfOp {
+  static constexpr int kDegree = MfDegree<B>::value;
   MfView V;
   MfTables T;
   __device__ __forceinline__ int64_t nslices() const { return V.nslices; }
@@ -118,7 +119,6 @@ struct MfOp {
         }
       }
     } else {
-    // ---- cell term by sum factorisation (index i = a + N b, qp = k + Q l)
     // ---- cell term by sum factorisation (index i = a + N b, qp = k + Q l)
     float tu[N][Q], td[N][Q];
 #pragma unroll
@@ -242,6 +242,254 @@ struct MfOp {
     }
   }
 };
+
+// 3D hexahedra (p = 1, 2), same scheme: cell term plane by plane (xi_2 Gauss
+// plane m outermost) with sum factorisation inside the plane; face terms
+// from the face traces of both sides. Planes and faces are loops at run time
+// (fully unrolled, the code outgrows the instruction cache). Both sides'
+// DoFs are read through strides set by the local face, and the flux
+// coefficients of each side are stored in that side's face frame (normal
+// axis, then the tangential axes in increasing order), so no register array
+// is indexed at run time. Index i = a + N b + N^2 c, qp = k + Q l + Q^2 m.
+template <int B> struct Mf3Degree;
+template <> struct Mf3Degree<8> { static constexpr int value = 1; };
+template <> struct Mf3Degree<27> { static constexpr int value = 2; };
+
+#ifndef AGG_MF3_MINB
+#define AGG_MF3_MINB 1
+#endif
+template <int B>
+struct MfOp3 {
+  static constexpr int kDegree = Mf3Degree<B>::value;
+  static constexpr int kMinBlocks = AGG_MF3_MINB;
+  MfView V;
+  MfTables T;
+  __device__ __forceinline__ int64_t nslices() const { return V.nslices; }
+
+  __device__ __forceinline__ void apply(int64_t slice, int lane, const float* __restrict__ x, float* acc) const {
+    constexpr int P = kDegree, N = P + 1, Q = P + 2, NN = N * N, QQ = Q * Q;
+    const int64_t unit = slice * SL + lane;
+    float u[B];
+#pragma unroll
+    for (int i = 0; i < B; ++i) u[i] = x[(size_t)unit * B + i];
+    const float* cd = V.cell + (size_t)slice * QQ * Q * 7 * SL + lane;
+    // ---- cell term
+#ifndef AGG_MF3_PLANE_UNROLL
+#define AGG_MF3_PLANE_UNROLL 1
+#endif
+    constexpr int kPlaneUnroll = AGG_MF3_PLANE_UNROLL;
+#pragma unroll kPlaneUnroll
+    for (int m = 0; m < Q; ++m) {
+      float Lm[N], Dm[N];
+#pragma unroll
+      for (int c = 0; c < N; ++c) {
+        Lm[c] = T.L[c][m];
+        Dm[c] = T.D[c][m];
+      }
+      float v[NN], w[NN];
+#pragma unroll
+      for (int ab = 0; ab < NN; ++ab) {
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+          s0 += Lm[c] * u[ab + NN * c];
+          s1 += Dm[c] * u[ab + NN * c];
+        }
+        v[ab] = s0;
+        w[ab] = s1;
+      }
+      float tu[N][Q], td[N][Q], tw[N][Q];
+#pragma unroll
+      for (int b = 0; b < N; ++b)
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+          float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+          for (int a = 0; a < N; ++a) {
+            s0 += T.L[a][k] * v[a + N * b];
+            s1 += T.D[a][k] * v[a + N * b];
+            s2 += T.L[a][k] * w[a + N * b];
+          }
+          tu[b][k] = s0;
+          td[b][k] = s1;
+          tw[b][k] = s2;
+        }
+      float p0[N][Q], p1[N][Q], p2[N][Q];
+#pragma unroll
+      for (int b = 0; b < N; ++b)
+#pragma unroll
+        for (int k = 0; k < Q; ++k) { p0[b][k] = 0.f; p1[b][k] = 0.f; p2[b][k] = 0.f; }
+#pragma unroll
+      for (int l = 0; l < Q; ++l)
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+          float uq = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+#pragma unroll
+          for (int b = 0; b < N; ++b) {
+            uq += T.L[b][l] * tu[b][k];
+            g0 += T.L[b][l] * td[b][k];
+            g1 += T.D[b][l] * tu[b][k];
+            g2 += T.L[b][l] * tw[b][k];
+          }
+          const float* gq = cd + (size_t)((k + Q * l + QQ * m) * 7) * SL;
+          const float G00 = __ldg(gq), G01 = __ldg(gq + SL), G02 = __ldg(gq + 2 * SL);
+          const float G11 = __ldg(gq + 3 * SL), G12 = __ldg(gq + 4 * SL), G22 = __ldg(gq + 5 * SL);
+          const float mm = __ldg(gq + 6 * SL);
+          const float w0 = G00 * g0 + G01 * g1 + G02 * g2;
+          const float w1 = G01 * g0 + G11 * g1 + G12 * g2;
+          const float w2 = G02 * g0 + G12 * g1 + G22 * g2;
+          const float wm = mm * uq;
+#pragma unroll
+          for (int b = 0; b < N; ++b) {
+            p0[b][k] += T.L[b][l] * w0;
+            p1[b][k] += T.D[b][l] * w1 + T.L[b][l] * wm;
+            p2[b][k] += T.L[b][l] * w2;
+          }
+        }
+#pragma unroll
+      for (int b = 0; b < N; ++b)
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+          float pv = 0.f, pw = 0.f;
+#pragma unroll
+          for (int k = 0; k < Q; ++k) {
+            pv += T.D[a][k] * p0[b][k] + T.L[a][k] * p1[b][k];
+            pw += T.L[a][k] * p2[b][k];
+          }
+#pragma unroll
+          for (int c = 0; c < N; ++c) acc[a + N * b + NN * c] += Lm[c] * pv + Dm[c] * pw;
+        }
+    }
+    // ---- face terms: one pass per face at run time; both sides' traces are
+    // read from memory through strides, the test-side sums go to the
+    // thread's column of a shared array (no register array is indexed at run
+    // time) and join acc at the end
+    constexpr int NT = UnitThreads<B>::value;
+    __shared__ float sacc[B][NT];
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < B; ++i) sacc[i][t] = 0.f;
+    const float* xe = x + (size_t)unit * B;
+#pragma unroll 1
+    for (int f = 0; f < 6; ++f) {
+      const size_t fi = ((size_t)slice * 6 + f) * SL + lane;
+      const int nb = V.nbr[fi];
+      if (nb < 0) continue;
+      const int fnb = V.code[fi];
+      float sU[N][Q], sT[N][Q], sN[N][Q], nU[N][Q], nT[N][Q], nN[N][Q];
+      face_trace(xe, f, sU, sT, sN);
+      face_trace(x + (size_t)nb * B, fnb, nU, nT, nN);
+      float rF[N][Q], rT[N][Q], rN[N][Q];
+#pragma unroll
+      for (int j2 = 0; j2 < N; ++j2)
+#pragma unroll
+        for (int q1 = 0; q1 < Q; ++q1) { rF[j2][q1] = 0.f; rT[j2][q1] = 0.f; rN[j2][q1] = 0.f; }
+      const float* fd = V.face + (size_t)((slice * 6 + f) * QQ * 7) * SL + lane;
+#pragma unroll
+      for (int q2 = 0; q2 < Q; ++q2)
+#pragma unroll
+        for (int q1 = 0; q1 < Q; ++q1) {
+          float up = 0.f, gt0 = 0.f, gt1 = 0.f, gnn = 0.f, um = 0.f, ht0 = 0.f, ht1 = 0.f, hn = 0.f;
+#pragma unroll
+          for (int j2 = 0; j2 < N; ++j2) {
+            up += T.L[j2][q2] * sU[j2][q1];
+            gt0 += T.L[j2][q2] * sT[j2][q1];
+            gt1 += T.D[j2][q2] * sU[j2][q1];
+            gnn += T.L[j2][q2] * sN[j2][q1];
+            um += T.L[j2][q2] * nU[j2][q1];
+            ht0 += T.L[j2][q2] * nT[j2][q1];
+            ht1 += T.D[j2][q2] * nU[j2][q1];
+            hn += T.L[j2][q2] * nN[j2][q1];
+          }
+          const float* fq = fd + (size_t)((q1 + Q * q2) * 7) * SL;
+          const float aN = __ldg(fq), aT0 = __ldg(fq + SL), aT1 = __ldg(fq + 2 * SL);
+          const float bN = __ldg(fq + 3 * SL), bT0 = __ldg(fq + 4 * SL), bT1 = __ldg(fq + 5 * SL);
+          const float sq = __ldg(fq + 6 * SL);
+          const float flux = aN * gnn + aT0 * gt0 + aT1 * gt1 + bN * hn + bT0 * ht0 + bT1 * ht1;
+          const float jump = up - um;
+          const float cf = -0.5f * flux + sq * jump;
+          const float hj = -0.5f * jump;
+#pragma unroll
+          for (int j2 = 0; j2 < N; ++j2) {
+            rF[j2][q1] += T.L[j2][q2] * cf + T.D[j2][q2] * (hj * aT1);
+            rT[j2][q1] += T.L[j2][q2] * (hj * aT0);
+            rN[j2][q1] += T.L[j2][q2] * (hj * aN);
+          }
+        }
+      // test side: face DoFs (value, tangential derivatives) and the normal
+      // derivative of every DoF behind each face node
+      const int KF = f >> 1, SF = f & 1;
+      const int SK = (KF == 0) ? 1 : (KF == 1 ? N : NN);
+      const int S0 = (KF == 0) ? N : 1, S1 = (KF == 2) ? N : NN;
+#pragma unroll
+      for (int j2 = 0; j2 < N; ++j2)
+#pragma unroll
+        for (int j1 = 0; j1 < N; ++j1) {
+          float ff = 0.f, fnrm = 0.f;
+#pragma unroll
+          for (int q1 = 0; q1 < Q; ++q1) {
+            ff += T.L[j1][q1] * rF[j2][q1] + T.D[j1][q1] * rT[j2][q1];
+            fnrm += T.L[j1][q1] * rN[j2][q1];
+          }
+          const int line = j1 * S0 + j2 * S1;
+#pragma unroll
+          for (int i = 0; i < N; ++i) {
+            const float de = SF ? T.Dend[1][i] : T.Dend[0][i];
+            const bool on_face = (SF ? P : 0) == i;
+            sacc[i * SK + line][t] += de * fnrm + (on_face ? ff : 0.f);
+          }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < B; ++i) acc[i] += sacc[i][t];
+  }
+
+  // Trace (U), derivative along the first tangential axis (Tn) and normal
+  // derivative (Nr) on local face f of the element whose DoFs start at xb,
+  // interpolated to the Gauss points along the first tangential axis and
+  // kept at the nodes along the second: [j2][q1].
+  __device__ __forceinline__ void face_trace(const float* __restrict__ xb, int f, float (&U)[kDegree + 1][kDegree + 2],
+                                             float (&Tn)[kDegree + 1][kDegree + 2],
+                                             float (&Nr)[kDegree + 1][kDegree + 2]) const {
+    constexpr int P = kDegree, N = P + 1, Q = P + 2, NN = N * N;
+    const int k = f >> 1, sd = f & 1;
+    const int SK = (k == 0) ? 1 : (k == 1 ? N : NN);
+    const int S0 = (k == 0) ? N : 1, S1 = (k == 2) ? N : NN;
+    const float* xf = xb + sd * P * SK;
+#pragma unroll
+    for (int j2 = 0; j2 < N; ++j2) {
+      float tr[N], dn[N];
+#pragma unroll
+      for (int j1 = 0; j1 < N; ++j1) {
+        float s = 0.f;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const float de = sd ? T.Dend[1][i] : T.Dend[0][i];
+          s += de * xb[i * SK + j1 * S0 + j2 * S1];
+        }
+        dn[j1] = s;
+        tr[j1] = xf[j1 * S0 + j2 * S1];
+      }
+#pragma unroll
+      for (int q1 = 0; q1 < Q; ++q1) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+        for (int j1 = 0; j1 < N; ++j1) {
+          a0 += T.L[j1][q1] * tr[j1];
+          a1 += T.D[j1][q1] * tr[j1];
+          a2 += T.L[j1][q1] * dn[j1];
+        }
+        U[j2][q1] = a0;
+        Tn[j2][q1] = a1;
+        Nr[j2][q1] = a2;
+      }
+    }
+  }
+};
+
+template <int B> struct MfOpFor { using type = MfOp<B>; };
+template <> struct MfOpFor<8> { using type = MfOp3<8>; };
+template <> struct MfOpFor<27> { using type = MfOp3<27>; };
 
 // Sliced block-sparse operator in the same interface.
 template <typename T, int B>

@@ -98,7 +98,7 @@ struct HierOptions {
 int hierarchy_build(const Mesh& m, double mass_coeff, const HierOptions& o, HostHierarchy& h,
                     std::string& err);
 
-// Quadrature data of the matrix-free fine operator (2D), elements in the
+// Quadrature data of the matrix-free fine operator, elements in the
 // order `perm` (internal -> element id), packed per slice of 32 elements:
 //   cell[slice][qp*4 + {G00, G01, G11, m}][lane]  with G = w |J| J^-1 D J^-T,
 //                                               m = c w |J|
@@ -106,6 +106,11 @@ int hierarchy_build(const Mesh& m, double mass_coeff, const HierOptions& o, Host
 //        b = wdS J_n^-1 D_n n (neighbour), s = wdS sigma  (n: e's outward normal)
 //   nbr[slice][f][lane]  neighbour's internal index or -1
 //   code[slice][f][lane] neighbour's local face * 2 + reversed
+// 3D hexahedra: cell[slice][qp*7 + {G00, G01, G02, G11, G12, G22, m}][lane],
+//   face[slice][f][q*7 + {aN, aT0, aT1, bN, bT0, bT1, s}][lane] with a and b in
+//   their side's face frame (its normal axis, then its tangential axes in
+//   increasing order), code = neighbour's local face; neighbours must
+//   parametrise a shared face alike (same corner order).
 struct MatrixFreeData {
   int q = 0;
   std::vector<float> cell, face;

@@ -607,9 +607,13 @@ void bsr_apply(const BlockCSR& A, const double* x, double* y) {
 
 namespace aggmg {
 
+static int matrix_free_build_3d(const Mesh& m, const std::vector<int64_t>& perm, const std::vector<int64_t>& inv,
+                                double c, MatrixFreeData& out, std::string& err);
+
 int matrix_free_build(const Mesh& m, const std::vector<int64_t>& perm, const std::vector<int64_t>& inv, double c,
                       MatrixFreeData& out, std::string& err) {
-  if (m.dim != 2) { err = "the matrix-free fine operator is built for 2D meshes"; return AGG_EUNSUPPORTED; }
+  if (m.dim == 3) return matrix_free_build_3d(m, perm, inv, c, out, err);
+  if (m.dim != 2) { err = "the matrix-free fine operator is built for 2D and 3D meshes"; return AGG_EUNSUPPORTED; }
   const int dim = 2, V = 4, nf = 4, p = m.p;
   const int q = p + 1 + m.quad_extra;
   const int Q = q * q;
@@ -715,6 +719,146 @@ int matrix_free_build(const Mesh& m, const std::vector<int64_t>& perm, const std
     }
   }
   if (bad) { err = "matrix-free geometry: bad Jacobian or non-matching face points"; return AGG_EINVAL; }
+  return AGG_OK;
+}
+
+
+// 3D: cell[slice][qp*7 + {G00, G01, G02, G11, G12, G22, m}][lane] at Q^3 points
+// (qp = k + Q l + Q^2 m'), face[slice][f][q*7 + {aN, aT0, aT1, bN, bT0, bT1, s}][lane]
+// at Q^2 points per face (q = q1 + Q q2 along the face's remaining axes in
+// increasing order; a and b in their side's face frame), code = neighbour's
+// local face. The neighbour's face must be parametrised the same way (matching
+// face-corner order); otherwise the matrix-free operator is unsupported.
+static int matrix_free_build_3d(const Mesh& m, const std::vector<int64_t>& perm, const std::vector<int64_t>& inv,
+                                double c, MatrixFreeData& out, std::string& err) {
+  const int dim = 3, V = 8, nf = 6, p = m.p;
+  const int q = p + 1 + m.quad_extra;
+  const int Q3 = q * q * q, Q2 = q * q;
+  const double c_pen = (m.penalty_mode == 0) ? double(p * (p + 1)) : m.penalty_coeff * p * p;
+  Tables1D t = make_tables(p, q);
+  const int64_t ne = m.ne;
+  const int64_t nsl = (ne + 31) / 32;
+  out.q = q;
+  out.cell.assign((size_t)nsl * 32 * Q3 * 7, 0.0f);
+  out.face.assign((size_t)nsl * 32 * nf * Q2 * 7, 0.0f);
+  out.nbr.assign((size_t)nsl * 32 * nf, -1);
+  out.code.assign((size_t)nsl * 32 * nf, 0);
+  int fcorn[6][4];
+  for (int f = 0; f < nf; ++f) face_corners(dim, f, fcorn[f]);
+  int bad = 0, misoriented = 0;
+#pragma omp parallel for schedule(static) reduction(+ : bad, misoriented)
+  for (int64_t r = 0; r < ne; ++r) {
+    const int64_t e = perm[r];
+    const int64_t sl = r / 32, lane = r % 32;
+    double Xe[8 * MAXD], Xn[8 * MAXD];
+    for (int cc = 0; cc < V; ++cc)
+      for (int k = 0; k < dim; ++k) Xe[cc * dim + k] = m.X[m.cells[e * V + cc] * dim + k];
+    const double* De = &m.D[e * 9];
+    for (int iq = 0; iq < Q3; ++iq) {
+      double xi[3] = {t.gx[iq % q], t.gx[(iq / q) % q], t.gx[iq / Q2]};
+      const double w = t.gw[iq % q] * t.gw[(iq / q) % q] * t.gw[iq / Q2];
+      double x[3], J[MAXD][MAXD], Ji[MAXD][MAXD];
+      map_point(dim, Xe, xi, x, J);
+      const double det = det_inv(dim, J, Ji);
+      if (!(det > 0)) bad += 1;
+      double G[3][3];
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          double sacc = 0.0;
+          for (int k = 0; k < 3; ++k)
+            for (int l = 0; l < 3; ++l) sacc += Ji[a][k] * De[k * 3 + l] * Ji[b][l];
+          G[a][b] = w * det * sacc;
+        }
+      const double vals[7] = {G[0][0], G[0][1], G[0][2], G[1][1], G[1][2], G[2][2], c * w * det};
+      for (int comp = 0; comp < 7; ++comp)
+        out.cell[((size_t)sl * Q3 * 7 + iq * 7 + comp) * 32 + lane] = (float)vals[comp];
+    }
+    for (int f = 0; f < nf; ++f) {
+      const int64_t rec = m.face_nbr[e * nf + f];
+      if (rec < 0) continue;
+      const int64_t n = rec / nf;
+      const int fn = (int)(rec % nf);
+      bool same = true;
+      for (int mm = 0; mm < 4; ++mm) same = same && (m.cells[n * V + fcorn[fn][mm]] == m.cells[e * V + fcorn[f][mm]]);
+      if (!same) {
+        misoriented += 1;
+        continue;
+      }
+      out.nbr[((size_t)sl * nf + f) * 32 + lane] = (int32_t)inv[n];
+      out.code[((size_t)sl * nf + f) * 32 + lane] = (int8_t)fn;
+      for (int cc = 0; cc < V; ++cc)
+        for (int k = 0; k < dim; ++k) Xn[cc * dim + k] = m.X[m.cells[n * V + cc] * dim + k];
+      const double* Dn = &m.D[n * 9];
+      const int kf = f / 2, sf = f % 2, kn = fn / 2, sn = fn % 2;
+      int oe[2], on[2], no = 0, nn = 0;
+      for (int a = 0; a < 3; ++a) {
+        if (a != kf) oe[no++] = a;
+        if (a != kn) on[nn++] = a;
+      }
+      double area = 0.0;
+      std::vector<double> av(Q2 * 3), bv(Q2 * 3), sg(Q2), wdS(Q2);
+      for (int iq = 0; iq < Q2; ++iq) {
+        const double t1 = t.gx[iq % q], t2 = t.gx[iq / q];
+        double xip[3], xim[3];
+        xip[kf] = sf;
+        xip[oe[0]] = t1;
+        xip[oe[1]] = t2;
+        xim[kn] = sn;
+        xim[on[0]] = t1;
+        xim[on[1]] = t2;
+        double xp[3], xm[3], Jp[MAXD][MAXD], Jm[MAXD][MAXD], Jip[MAXD][MAXD], Jim[MAXD][MAXD];
+        map_point(dim, Xe, xip, xp, Jp);
+        map_point(dim, Xn, xim, xm, Jm);
+        const double detp = det_inv(dim, Jp, Jip);
+        det_inv(dim, Jm, Jim);
+        double dist = 0.0, scale = 1.0;
+        for (int k = 0; k < 3; ++k) {
+          dist = std::max(dist, std::fabs(xp[k] - xm[k]));
+          scale = std::max(scale, std::fabs(xp[k]));
+        }
+        if (dist > 1e-10 * scale) bad += 1;
+        double nv[3], len = 0.0;
+        for (int k = 0; k < 3; ++k) {
+          nv[k] = Jip[kf][k] * (2.0 * sf - 1.0);
+          len += nv[k] * nv[k];
+        }
+        len = std::sqrt(len);
+        const double nu[3] = {nv[0] / len, nv[1] / len, nv[2] / len};
+        wdS[iq] = t.gw[iq % q] * t.gw[iq / q] * detp * len;
+        area += wdS[iq];
+        double Den[3], Dnn[3];
+        for (int k = 0; k < 3; ++k) {
+          Den[k] = De[k * 3 + 0] * nu[0] + De[k * 3 + 1] * nu[1] + De[k * 3 + 2] * nu[2];
+          Dnn[k] = Dn[k * 3 + 0] * nu[0] + Dn[k * 3 + 1] * nu[1] + Dn[k * 3 + 2] * nu[2];
+        }
+        // a and b in their side's face frame (normal axis, then the two tangential
+        // axes in increasing order)
+        const int eframe[3] = {kf, oe[0], oe[1]}, nframe[3] = {kn, on[0], on[1]};
+        for (int a = 0; a < 3; ++a) {
+          const int ae = eframe[a];
+          av[iq * 3 + a] = wdS[iq] * (Jip[ae][0] * Den[0] + Jip[ae][1] * Den[1] + Jip[ae][2] * Den[2]);
+          const int an = nframe[a];
+          bv[iq * 3 + a] = wdS[iq] * (Jim[an][0] * Dnn[0] + Jim[an][1] * Dnn[1] + Jim[an][2] * Dnn[2]);
+        }
+        double nDn = 0.0;
+        for (int k = 0; k < 3; ++k)
+          for (int l = 0; l < 3; ++l) nDn += nu[k] * 0.5 * (De[k * 3 + l] + Dn[k * 3 + l]) * nu[l];
+        sg[iq] = nDn;
+      }
+      const double alpha = c_pen * std::max(area / m.vol[e], area / m.vol[n]);
+      for (int iq = 0; iq < Q2; ++iq) {
+        const double vals[7] = {av[iq * 3], av[iq * 3 + 1], av[iq * 3 + 2], bv[iq * 3], bv[iq * 3 + 1],
+                                bv[iq * 3 + 2], wdS[iq] * alpha * sg[iq]};
+        for (int comp = 0; comp < 7; ++comp)
+          out.face[(((size_t)sl * nf + f) * Q2 * 7 + iq * 7 + comp) * 32 + lane] = (float)vals[comp];
+      }
+    }
+  }
+  if (bad) { err = "matrix-free geometry: bad Jacobian or non-matching face points"; return AGG_EINVAL; }
+  if (misoriented) {
+    err = "matrix-free operator (3D) needs neighbours that parametrise shared faces alike";
+    return AGG_EUNSUPPORTED;
+  }
   return AGG_OK;
 }
 

@@ -1,6 +1,9 @@
-"""Matrix-free fine operator (float32, 2D) of the V-cycle against the oracle's
-assembled float64 operator, and the solver built on it against the float64
-oracle (the float32 V-cycle tolerance and the 1e-8 trajectory bound)."""
+"""Matrix-free fine operator (float32; quadrilaterals and hexahedra) of the
+V-cycle against the oracle's assembled float64 operator, and the solver built
+on it against the float64 oracle (the float32 V-cycle tolerance and the 1e-8
+trajectory bound)."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -31,7 +34,23 @@ CASES = {
     "jsquare2d_q2_30": lambda: W.jittered_square_2d(n=30, degree=2, n_levels=3),
     "jsquare2d_q3_18": lambda: W.jittered_square_2d(n=18, degree=3, n_levels=2),
     "square2d_q1_16": lambda: W.square_2d_fhn(16, 1),
+    "jcube3d_q1_6": lambda: W.jittered_cube_3d(n=6, degree=1, n_levels=3, group=2),
+    "jcube3d_q2_6": lambda: W.jittered_cube_3d(n=6, degree=2, n_levels=3, group=2),
+    "shell_q2": lambda: W.ventricle_shell(16, 8, 4, n_levels=3),
 }
+
+
+def _rotated_element_cube():
+    """6^3 jittered Q2 cube whose element 0 lists its corners rotated by 90
+    degrees about the z axis: a valid mesh whose shared faces of element 0
+    are parametrised differently by the two sides."""
+    wl = W.jittered_cube_3d(n=6, degree=2, n_levels=3, group=2)
+    el = wl.mesh.elements.copy()
+    old = el[0].copy()
+    for c in range(8):
+        i, j, k = c & 1, (c >> 1) & 1, (c >> 2) & 1
+        el[0, c] = old[(1 - j) | (i << 1) | (k << 2)]
+    return dataclasses.replace(wl, mesh=dataclasses.replace(wl.mesh, elements=el))
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -75,9 +94,17 @@ def test_matrix_free_vcycle_and_trajectory(name):
 
 def test_matrix_free_rejected_where_unsupported():
     from paper_2602_16312_gb300 import aggmg
-    wl = W.jittered_cube_3d(n=4, degree=1, n_levels=2, group=2)
+    wl = W.jittered_cube_3d(n=4, degree=3, n_levels=2, group=2)
     with pytest.raises(aggmg.AggError) as e:
         aggmg.Hierarchy(aggmg.Mesh.from_workload(wl), 1.0 / wl.dt, wl.maps, precision="f32", fine="mf")
+    assert e.value.status == aggmg.AGG_EUNSUPPORTED
+    # shared faces parametrised differently by the two sides: the assembled
+    # operator takes the mesh, the 3D matrix-free one reports it unsupported
+    wl = _rotated_element_cube()
+    mesh = aggmg.Mesh.from_workload(wl)
+    aggmg.Hierarchy(mesh, 1.0 / wl.dt, wl.maps, precision="f32").close()
+    with pytest.raises(aggmg.AggError) as e:
+        aggmg.Hierarchy(mesh, 1.0 / wl.dt, wl.maps, precision="f32", fine="mf")
     assert e.value.status == aggmg.AGG_EUNSUPPORTED
     wl = W.jittered_square_2d(n=8, degree=2, n_levels=2)
     with pytest.raises(aggmg.AggError) as e:
