@@ -94,9 +94,11 @@ template <int B> struct UnitThreads {
 };
 
 // Minimum resident blocks per SM asked of the compiler for the kernels that
-// evaluate an operator Op: Op::kMinBlocks where Op has it, else 1.
+// evaluate an operator Op: Op::kMinBlocks where Op has it, else 0 (0 leaves
+// the register budget to the compiler's own heuristics, as if no minimum
+// were given; an explicit 1 lets it take up to 255 registers).
 template <typename Op, typename = void> struct OpMinBlocks {
-  static constexpr int value = 1;
+  static constexpr int value = 0;
 };
 template <typename Op> struct OpMinBlocks<Op, std::void_t<decltype(Op::kMinBlocks)>> {
   static constexpr int value = Op::kMinBlocks;

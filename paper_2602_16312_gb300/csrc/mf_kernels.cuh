@@ -256,7 +256,7 @@ template <> struct Mf3Degree<8> { static constexpr int value = 1; };
 template <> struct Mf3Degree<27> { static constexpr int value = 2; };
 
 #ifndef AGG_MF3_MINB
-#define AGG_MF3_MINB 1
+#define AGG_MF3_MINB 0
 #endif
 template <int B>
 struct MfOp3 {
