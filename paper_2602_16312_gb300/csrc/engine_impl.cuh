@@ -19,6 +19,7 @@
 #include "cg_kernels.cuh"
 #include "engine.h"
 #include "kernels.cuh"
+#include "face_op.cuh"
 #include "mf_kernels.cuh"
 #include "coarse_kernels.cuh"
 
@@ -87,7 +88,15 @@ class Engine : public EngineBase {
     return std::max<int64_t>(1, cdiv(nsl * SL, NTB));
   }
   int nlev_ = 0, degree_ = 3;
-  SellView<double> A0_{};
+  // level 0 in face-structured form: float64 for the outer CG, and the
+  // V-cycle precision copy for the assembled smoother (the same data when
+  // the V-cycle is float64)
+  using A0Op = FaceOp<double, B>;
+  using L0Op = FaceOp<T, B>;
+  A0Op A0f_{};
+  L0Op fop_{};
+  double face_entries_ = 0;          // stored operator entries of level 0
+  SellView<double> A0_{};            // slot structure of level 0 (adjoint face data), no values
   double* Me_ = nullptr;
   double *Linv_ = nullptr, *U_ = nullptr, *yc_ = nullptr;
   int64_t nc_ = 0;
@@ -150,7 +159,8 @@ class Engine : public EngineBase {
   }
 
   template <typename TS>
-  int upload_sell(const BlockCSR& A, int64_t nsl, int32_t** sp, int32_t** cols, TS** vals, std::string& err) {
+  int upload_sell(const BlockCSR& A, int64_t nsl, int32_t** sp, int32_t** cols, TS** vals, std::string& err,
+                  bool with_vals = true) {
     constexpr int KP = Pad<TS, B>::KP;
     const int64_t n = A.nrows;
     std::vector<int32_t> hsp(nsl + 1, 0);
@@ -162,7 +172,7 @@ class Engine : public EngineBase {
     }
     const int64_t nslots = hsp[nsl];
     std::vector<int32_t> hc((size_t)nslots * SL, 0);
-    std::vector<TS> hv((size_t)nslots * SL * KP, to_storage<TS>(0.0));
+    std::vector<TS> hv(with_vals ? (size_t)nslots * SL * KP : 0, to_storage<TS>(0.0));
     for (int64_t s = 0; s < nsl; ++s)
       for (int lane = 0; lane < SL; ++lane) {
         const int64_t u = s * SL + lane;
@@ -172,7 +182,7 @@ class Engine : public EngineBase {
           if (j < len) {
             const int64_t k = A.rowptr[u] + j;
             hc[slot * SL + lane] = A.col[k];
-            pack<TS>(&A.val[(size_t)k * B * B], &hv[(size_t)slot * SL * KP], lane);
+            if (with_vals) pack<TS>(&A.val[(size_t)k * B * B], &hv[(size_t)slot * SL * KP], lane);
           } else {
             hc[slot * SL + lane] = (int32_t)(u < n ? u : 0);
           }
@@ -180,8 +190,49 @@ class Engine : public EngineBase {
       }
     int s = upload(sp, hsp.data(), hsp.size(), err);
     if (!s) s = upload(cols, hc.data(), hc.size(), err);
-    if (!s) s = upload(vals, hv.data(), hv.size(), err);
+    if (!s && with_vals) s = upload(vals, hv.data(), hv.size(), err);
     return s;
+  }
+
+  // ROWS x COLS row-major block -> sliced column-major chunks (k = c ROWS + r)
+  template <typename TS>
+  static void pack_rect(const double* blk, TS* slot_base, int lane, int rows, int cols) {
+    constexpr int VW = Vec<TS>::W;
+    for (int k = 0; k < rows * cols; ++k) {
+      const int c = k / rows, r = k % rows;
+      slot_base[((size_t)(k / VW) * SL + lane) * VW + (k % VW)] = to_storage<TS>(blk[r * cols + c]);
+    }
+  }
+
+  template <typename TS>
+  int upload_face(const FaceBlocks& fb, int64_t n, int64_t nsl, FaceOp<TS, B>& op, std::string& err) {
+    using F = FaceOp<TS, B>;
+    const int nf = F::NFACE, NF = F::NF, BO = F::BO;
+    std::vector<TS> hv((size_t)nsl * SL * F::KS, to_storage<TS>(0.0));
+    std::vector<int32_t> hn((size_t)nsl * nf * SL, -1);
+    std::vector<int8_t> hc((size_t)nsl * nf * SL, 0);
+    for (int64_t u = 0; u < n; ++u) {
+      const int64_t sl = u / SL;
+      const int lane = (int)(u % SL);
+      TS* sb = &hv[(size_t)sl * SL * F::KS];
+      pack_rect<TS>(&fb.diag[(size_t)u * B * B], sb, lane, B, B);
+      for (int f = 0; f < nf; ++f) {
+        TS* rb = sb + (size_t)SL * (F::KP + f * (F::KR + F::KC));
+        pack_rect<TS>(&fb.R[((size_t)u * nf + f) * NF * B], rb, lane, NF, B);
+        pack_rect<TS>(&fb.C[((size_t)u * nf + f) * BO * NF], rb + (size_t)SL * F::KR, lane, BO, NF);
+        hn[((size_t)sl * nf + f) * SL + lane] = fb.nbr[(size_t)u * nf + f];
+        hc[((size_t)sl * nf + f) * SL + lane] = fb.code[(size_t)u * nf + f];
+      }
+    }
+    TS* vals;
+    int32_t* nbr;
+    int8_t* code;
+    int rc;
+    if ((rc = upload(&vals, hv.data(), hv.size(), err))) return rc;
+    if ((rc = upload(&nbr, hn.data(), hn.size(), err))) return rc;
+    if ((rc = upload(&code, hc.data(), hc.size(), err))) return rc;
+    op.V = FaceView<TS, B>{vals, nbr, code, nsl};
+    return AGG_OK;
   }
 
   // B x B row-major blocks -> column-major copies in storage type TS
@@ -221,6 +272,7 @@ class Engine : public EngineBase {
     if constexpr (kRL) {
       if (l > 0) return vc_rowlane(l, s);
     }
+    if (l == 0) return vc_level(l, fop_, s);
     return vc_level(l, SellOp<T, B>{v.A()}, s);
   }
 
@@ -297,14 +349,14 @@ class Engine : public EngineBase {
 
   void launch_init(cudaStream_t s, unsigned long long cond, int use_cond) {
     k_cg_begin<<<1, 1, 0, s>>>(st_, cond, use_cond);
-    k_spmv<double, B, 1><<<bgrid(k_spmv<double, B, 1>, lev_[0].nsl), NTB, 0, s>>>(A0_, x_, b_, r_, nullptr, nullptr);
+    k_spmv<double, B, 1, A0Op><<<bgrid(0, lev_[0].nsl), NTB, 0, s>>>(A0f_, x_, b_, r_, nullptr, nullptr);
     k_r0<<<RED_BLOCKS, RED_NT, 0, s>>>(r_, N0(), partials_, st_);
     launch_precond(s, true);
     k_loop_ctl<<<1, 1, 0, s>>>(st_);
   }
 
   void launch_body(cudaStream_t s) {
-    k_spmv<double, B, 2><<<bgrid(k_spmv<double, B, 2>, lev_[0].nsl), NTB, 0, s>>>(A0_, p_, nullptr, q_, partials_, st_);
+    k_spmv<double, B, 2, A0Op><<<bgrid(0, lev_[0].nsl), NTB, 0, s>>>(A0f_, p_, nullptr, q_, partials_, st_);
     k_cg_update<<<RED_BLOCKS, RED_NT, 0, s>>>(x_, r_, p_, q_, N0(), partials_, st_);
     launch_precond(s, false);
     k_loop_ctl<<<1, 1, 0, s>>>(st_);
@@ -433,7 +485,8 @@ class Engine : public EngineBase {
       if ((rc = upload(&v.perm, hl.perm.data(), hl.perm.size(), err))) return rc;
       const bool coarsest = (l == nlev_ - 1);
       if (!coarsest) {
-        if ((rc = upload_sell<T>(hl.A, v.nsl, &v.slice_ptr, &v.cols, &v.vals, err))) return rc;
+        // level 0 keeps its slot structure only (its operator is face-structured)
+        if ((rc = upload_sell<T>(hl.A, v.nsl, &v.slice_ptr, &v.cols, &v.vals, err, l > 0))) return rc;
         if ((rc = upload_blocks<TD>(hl.Dinv, hl.n, v.nsl, &v.Dinv, err))) return rc;
         if ((rc = upload_blocks<T>(hl.P, hl.n, v.nsl, &v.P, err))) return rc;
         std::vector<int32_t> par(v.nsl * SL, 0);
@@ -473,14 +526,25 @@ class Engine : public EngineBase {
       }
       if ((rc = dalloc(&v.xa, v.nvec, err))) return rc;
     }
-    // float64 fine operator of the outer CG
-    if (std::is_same<T, double>::value && nlev_ > 1) {
-      A0_ = SellView<double>{lev_[0].slice_ptr, lev_[0].cols, reinterpret_cast<double*>(lev_[0].vals), lev_[0].nsl};
-    } else {
-      int32_t *sp, *cols;
-      double* vals;
-      if ((rc = upload_sell<double>(h.lev[0].A, lev_[0].nsl, &sp, &cols, &vals, err))) return rc;
-      A0_ = SellView<double>{sp, cols, vals, lev_[0].nsl};
+    // face-structured level-0 operators: float64 (outer CG) and, for the
+    // assembled smoother, the V-cycle precision
+    {
+      FaceBlocks fb;
+      if ((rc = face_blocks_build(m, h.lev[0], fb, err))) return rc;
+      int64_t nface = 0;
+      for (int32_t nb : fb.nbr) nface += (nb >= 0);
+      face_entries_ = (double)m.ne * B * B + (double)nface * (2.0 * fb.NF * B - (double)fb.NF * fb.NF);
+      if ((rc = upload_face<double>(fb, m.ne, lev_[0].nsl, A0f_, err))) return rc;
+      if constexpr (std::is_same<T, double>::value) {
+        fop_ = A0f_;
+      } else if (fine_operator != 1) {
+        if ((rc = upload_face<T>(fb, m.ne, lev_[0].nsl, fop_, err))) return rc;
+      }
+      if (!lev_[0].slice_ptr) {
+        if ((rc = upload_sell<double>(h.lev[0].A, lev_[0].nsl, &lev_[0].slice_ptr, &lev_[0].cols, nullptr, err, false)))
+          return rc;
+      }
+      A0_ = SellView<double>{lev_[0].slice_ptr, lev_[0].cols, nullptr, lev_[0].nsl};
     }
     // element mass blocks in internal order for the right-hand side
     {
@@ -627,7 +691,7 @@ class Engine : public EngineBase {
       if (use_mf0())
         k_op_apply<T, B, MfOpT><<<bgrid(0, v.nsl), NTB, 0, s>>>(mfop_, v.xa, v.xb);
       else
-        k_op_apply<T, B, SellOp<T, B>><<<bgrid(0, v.nsl), NTB, 0, s>>>(SellOp<T, B>{v.A()}, v.xa, v.xb);
+        k_op_apply<T, B, L0Op><<<bgrid(0, v.nsl), NTB, 0, s>>>(fop_, v.xa, v.xb);
       k_scatter_units<double, T><<<g, 256, 0, s>>>(v.xb, y_user, v.perm, v.n, B);
       AGG_CK(cudaGetLastError());
       return AGG_OK;
@@ -637,12 +701,12 @@ class Engine : public EngineBase {
     const int64_t g = cdiv(v.n * B, 256);
     if (l == 0) {
       k_gather_units<double, double><<<g, 256, 0, s>>>(x_user, p_, v.perm, v.n, B);
-      k_spmv<double, B, 0><<<bgrid(k_spmv<double, B, 0>, v.nsl), NTB, 0, s>>>(A0_, p_, nullptr, q_, nullptr, nullptr);
+      k_spmv<double, B, 0, A0Op><<<bgrid(0, v.nsl), NTB, 0, s>>>(A0f_, p_, nullptr, q_, nullptr, nullptr);
       k_scatter_units<double, double><<<g, 256, 0, s>>>(q_, y_user, v.perm, v.n, B);
     } else {
       if (l == nlev_ - 1) { err = "the coarsest level is applied through its Cholesky factor only"; return AGG_EUNSUPPORTED; }
       k_gather_units<T, double><<<g, 256, 0, s>>>(x_user, v.xa, v.perm, v.n, B);
-      k_spmv<T, B, 0><<<bgrid(k_spmv<T, B, 0>, v.nsl), NTB, 0, s>>>(v.A(), v.xa, nullptr, v.xb, nullptr, nullptr);
+      k_spmv<T, B, 0, SellOp<T, B>><<<bgrid(0, v.nsl), NTB, 0, s>>>(SellOp<T, B>{v.A()}, v.xa, nullptr, v.xb, nullptr, nullptr);
       k_scatter_units<double, T><<<g, 256, 0, s>>>(v.xb, y_user, v.perm, v.n, B);
     }
     AGG_CK(cudaGetLastError());
@@ -676,13 +740,13 @@ class Engine : public EngineBase {
       double* xi = static_cast<double*>(s_in);
       double* yi = static_cast<double*>(s_out);
       k_gather_units<double, double><<<g, 256, 0, s>>>(x_user, xi, v.perm, v.n, B);
-      k_spmv<double, B, 0><<<bgrid(k_spmv<double, B, 0>, v.nsl), NTB, 0, s>>>(A0_, xi, nullptr, yi, nullptr, nullptr);
+      k_spmv<double, B, 0, A0Op><<<bgrid(0, v.nsl), NTB, 0, s>>>(A0f_, xi, nullptr, yi, nullptr, nullptr);
       k_scatter_units<double, double><<<g, 256, 0, s>>>(yi, y_user, v.perm, v.n, B);
     } else {
       T* xi = static_cast<T*>(s_in);
       T* yi = static_cast<T*>(s_out);
       k_gather_units<T, double><<<g, 256, 0, s>>>(x_user, xi, v.perm, v.n, B);
-      k_spmv<T, B, 0><<<bgrid(k_spmv<T, B, 0>, v.nsl), NTB, 0, s>>>(v.A(), xi, nullptr, yi, nullptr, nullptr);
+      k_spmv<T, B, 0, SellOp<T, B>><<<bgrid(0, v.nsl), NTB, 0, s>>>(SellOp<T, B>{v.A()}, xi, nullptr, yi, nullptr, nullptr);
       k_scatter_units<double, T><<<g, 256, 0, s>>>(yi, y_user, v.perm, v.n, B);
     }
     AGG_CK(cudaGetLastError());
@@ -747,7 +811,7 @@ class Engine : public EngineBase {
       IonicParams ip{sp_.model, sp_.k, sp_.a, sp_.eps, sp_.gamma, sp_.mu1, sp_.mu2};
       const double c = 1.5 * sp_.chi * sp_.cm / sp_.dt;
       const double ia = (clock < sp_.iapp_steps) ? sp_.iapp_value : 0.0;
-      k_spmv<double, B, 0><<<bgrid(0, v0.nsl), NTB, 0, s>>>(A0_, x_, nullptr, q_, nullptr, nullptr);
+      k_spmv<double, B, 0, A0Op><<<bgrid(0, v0.nsl), NTB, 0, s>>>(A0f_, x_, nullptr, q_, nullptr, nullptr);
       k_bdf2_start<B><<<bgrid(0, v0.nsl), NTB, 0, s>>>(Minv_, q_, x_, w_, mask_, up_, wp_, ip, sp_.dt, sp_.chi, sp_.cm,
                                                        c, ia, v0.nsl);
       hist_valid_ = true;
@@ -786,22 +850,21 @@ class Engine : public EngineBase {
     for (int i = 0; i < reps; ++i) {
       switch (id) {
         case 0:
-          k_spmv<double, B, 0><<<bgrid(k_spmv<double, B, 0>, n), NTB, 0, s>>>(A0_, p_, nullptr, q_, nullptr, nullptr);
+          k_spmv<double, B, 0, A0Op><<<bgrid(0, n), NTB, 0, s>>>(A0f_, p_, nullptr, q_, nullptr, nullptr);
           break;
         case 1:
           if (use_mf0())
             k_cheb<T, TD, B, 2, MfOpT><<<bgrid(0, n), NTB, 0, s>>>(mfop_, v.Dinv, v.rhs, v.xa, v.xb, v.d, v.c1[1],
                                                                    v.c2[1], v.nsl, nullptr);
           else
-            k_cheb<T, TD, B, 2, SellOp<T, B>><<<bgrid(0, n), NTB, 0, s>>>(SellOp<T, B>{v.A()}, v.Dinv, v.rhs, v.xa,
-                                                                          v.xb, v.d, v.c1[1], v.c2[1], v.nsl, nullptr);
+            k_cheb<T, TD, B, 2, L0Op><<<bgrid(0, n), NTB, 0, s>>>(fop_, v.Dinv, v.rhs, v.xa, v.xb, v.d, v.c1[1],
+                                                                  v.c2[1], v.nsl, nullptr);
           break;
         case 2:
           if (use_mf0())
             k_resid_restrict<T, B, MfOpT><<<bgrid(0, n), NTB, 0, s>>>(mfop_, v.P, v.rhs, v.xa, v.S, nullptr);
           else
-            k_resid_restrict<T, B, SellOp<T, B>><<<bgrid(0, n), NTB, 0, s>>>(SellOp<T, B>{v.A()}, v.P, v.rhs, v.xa,
-                                                                             v.S, nullptr);
+            k_resid_restrict<T, B, L0Op><<<bgrid(0, n), NTB, 0, s>>>(fop_, v.P, v.rhs, v.xa, v.S, nullptr);
           break;
         case 3:
           k_prolong<T, B><<<bgrid(k_prolong<T, B>, n), NTB, 0, s>>>(v.P, v.parent, lev_[1].xa, v.xb, v.nsl, nullptr);
@@ -814,17 +877,21 @@ class Engine : public EngineBase {
   }
 
   int kernel_cost(int id, double& bytes, double& flops) const override {
-    const double n0 = (double)lev_[0].n, N = n0 * B, nz = (double)nnzb_[0], bb = (double)B * B;
+    const double n0 = (double)lev_[0].n, N = n0 * B, bb = (double)B * B;
     const double sT = sizeof(T), sD = sizeof(TD);
+    // face-structured operator: its stored entries and, per face slot, a
+    // neighbour id and a face code
+    const double fidx = n0 * 2 * FaceShape<B>::D * 5.0;
+    const double fe = face_entries_;
     switch (id) {
-      case 0: bytes = nz * (bb * 8 + 4) + 2 * N * 8; flops = 2 * nz * bb; break;
+      case 0: bytes = fe * 8 + fidx + 2 * N * 8; flops = 2 * fe; break;
       case 1:
-        bytes = (use_mf0() ? (double)mf_bytes_ : nz * (bb * sT + 4)) + n0 * bb * sD + 5 * N * sT;
-        flops = 2 * nz * bb + 2 * n0 * bb + 4 * N;
+        bytes = (use_mf0() ? (double)mf_bytes_ : fe * sT + fidx) + n0 * bb * sD + 5 * N * sT;
+        flops = 2 * fe + 2 * n0 * bb + 4 * N;
         break;
       case 2:
-        bytes = (use_mf0() ? (double)mf_bytes_ : nz * (bb * sT + 4)) + n0 * bb * sT + 3 * N * sT;
-        flops = 2 * nz * bb + 2 * n0 * bb + N;
+        bytes = (use_mf0() ? (double)mf_bytes_ : fe * sT + fidx) + n0 * bb * sT + 3 * N * sT;
+        flops = 2 * fe + 2 * n0 * bb + N;
         break;
       case 3: bytes = n0 * bb * sT + 2 * N * sT + (double)lev_[1].n * B * sT + n0 * 4; flops = 2 * n0 * bb + N; break;
       default: return AGG_EINVAL;

@@ -283,21 +283,21 @@ __device__ __forceinline__ double sum_partials(const double* partials, int n) {
 
 // ---------------------------------------------------------------- SpMV
 // MODE 0: y = A x;  MODE 1: y = rhs - A x;  MODE 2: y = A x and (x, y) -> alpha
-template <typename T, int B, int MODE>
-static __global__ void __launch_bounds__(UnitThreads<B>::value)
-    k_spmv(SellView<T> A, const T* __restrict__ x, const T* __restrict__ rhs, T* __restrict__ y, double* partials,
+template <typename T, int B, int MODE, typename Op>
+static __global__ void __launch_bounds__(UnitThreads<B>::value, OpMinBlocks<Op>::value)
+    k_spmv(Op A, const T* __restrict__ x, const T* __restrict__ rhs, T* __restrict__ y, double* partials,
            CGState* st) {
   constexpr int NTB = UnitThreads<B>::value;
   if (st && st->done) return;
   const int lane = threadIdx.x & 31;
   double part = 0.0;
   const int64_t slice = first_slice<NTB>();
-  if (slice < A.nslices) {
+  if (slice < A.nslices()) {
     const int64_t unit = slice * SL + lane;
     T acc[B];
 #pragma unroll
     for (int r = 0; r < B; ++r) acc[r] = T(0);
-    sell_row<T, B>(A, slice, lane, x, acc);
+    A.apply(slice, lane, x, acc);
     T* yb = y + (size_t)unit * B;
 #pragma unroll
     for (int r = 0; r < B; ++r) {

@@ -51,6 +51,9 @@ struct Mesh {
   // the opposite direction (2D)
   std::vector<int64_t> face_nbr;
   std::vector<int8_t> face_rev;
+  // face_slot[e*2d + f]: block of row e (offset from A.rowptr[e]) that holds
+  // the coupling through face f alone (-1 on the boundary)
+  std::vector<int32_t> face_slot;
   std::vector<double> Ke;        // [ne][B][B]
   std::vector<double> Y;         // [nnzb][4][B][B]
 };
@@ -119,6 +122,25 @@ struct MatrixFreeData {
 };
 int matrix_free_build(const Mesh& m, const std::vector<int64_t>& perm, const std::vector<int64_t>& inv, double c,
                       MatrixFreeData& out, std::string& err);
+
+// Level-0 operator c M + A in face-structured form, internal order: the
+// dense diagonal block of each element and, per local face f with neighbour
+// n, the two parts of the coupling block that can be nonzero for a GLL nodal
+// basis (a basis function whose node is off a face vanishes on it):
+//   R[f]: rows = e's DoFs on face f (r = j1 + N j2 over the face's
+//         tangential axes in increasing order), columns = all DoFs of n;
+//   C[f]: rows = e's other DoFs (r = j1 + N j2 + N^(d-1) i', i' the index
+//         along the normal axis with the face layer left out), columns =
+//         n's DoFs on its face fn (same face order).
+// All blocks row-major doubles; nbr = internal neighbour or -1, code = fn.
+struct FaceBlocks {
+  int NF = 0, nf = 0;
+  std::vector<double> diag, R, C;     // [n][B*B], [n][nf][NF*B], [n][nf][(B-NF)*NF]
+  std::vector<int32_t> nbr;           // [n][nf]
+  std::vector<int8_t> code;           // [n][nf]
+};
+// Fails (AGG_EINVAL) if an entry outside these parts is nonzero.
+int face_blocks_build(const Mesh& m, const HostLevel& l0, FaceBlocks& out, std::string& err);
 
 // inverses of n SPD B x B row-major blocks (Cholesky); false if one is not SPD
 bool spd_inverse_blocks(const double* blocks, int64_t n, int B, double* out);

@@ -360,6 +360,7 @@ int mesh_build(Mesh& m, std::string& err) {
   const int64_t nnzb = m.A.rowptr[ne];
   m.A.col.assign(nnzb, 0);
   m.A.val.assign((size_t)nnzb * B * B, 0.0);
+  m.face_slot.assign((size_t)ne * nf, -1);
   if (adj) m.Y.assign((size_t)nnzb * 4 * B * B, 0.0);
   int bad_face = 0;
 
@@ -387,6 +388,7 @@ int mesh_build(Mesh& m, std::string& err) {
       slot_of[ord[s]] = s;
       if (ord[s] == 0) diag_slot = s;
     }
+    for (int i = 1; i < nc; ++i) m.face_slot[e * nf + fof[i]] = (int32_t)slot_of[i];
     double* Adiag = &m.A.val[(size_t)(base + diag_slot) * B * B];
     std::memcpy(Adiag, &Ke[(size_t)e * B * B], sizeof(double) * B * B);
 
@@ -432,6 +434,10 @@ int mesh_build(Mesh& m, std::string& err) {
           for (int j = 0; j < dim - 1; ++j) Nf *= ((mm >> j) & 1) ? tq[j] : 1.0 - tq[j];
           for (int k = 0; k < dim; ++k) xim[k] += Nf * cxi[mm][k];
         }
+        // the neighbour's normal coordinate is constant on its face: set it
+        // exactly, so that its basis functions with nodes off the face vanish
+        // there exactly (the interpolated value is off by rounding)
+        xim[fn / 2] = (double)(fn % 2);
         double xp[MAXD], xm[MAXD], Jp[MAXD][MAXD], Jm[MAXD][MAXD], Jip[MAXD][MAXD], Jim[MAXD][MAXD];
         map_point(dim, Xp, xip, xp, Jp);
         map_point(dim, Xm, xim, xm, Jm);
@@ -858,6 +864,80 @@ static int matrix_free_build_3d(const Mesh& m, const std::vector<int64_t>& perm,
   if (misoriented) {
     err = "matrix-free operator (3D) needs neighbours that parametrise shared faces alike";
     return AGG_EUNSUPPORTED;
+  }
+  return AGG_OK;
+}
+
+
+// ---------------------------------------------------------------- face-structured operator
+namespace {
+int axis_stride(int N, int a) { return a == 0 ? 1 : (a == 1 ? N : N * N); }
+// r-th DoF on local face f (r = j1 + N j2 over the tangential axes in increasing order)
+int face_dof(int dim, int N, int f, int r) {
+  const int k = f / 2, s = f % 2;
+  int t[2] = {0, 0}, no = 0;
+  for (int a = 0; a < dim; ++a)
+    if (a != k) t[no++] = a;
+  int idx = s * (N - 1) * axis_stride(N, k) + (r % N) * axis_stride(N, t[0]);
+  if (dim == 3) idx += (r / N) * axis_stride(N, t[1]);
+  return idx;
+}
+// r-th DoF off local face f (r = j1 + N j2 + NF i', i' the normal index with
+// the face layer left out)
+int off_dof(int dim, int N, int f, int r) {
+  const int k = f / 2, s = f % 2, NF = dim == 2 ? N : N * N;
+  return (r / NF + 1 - s) * axis_stride(N, k) + face_dof(dim, N, 2 * k, r % NF);
+}
+}  // namespace
+
+int face_blocks_build(const Mesh& m, const HostLevel& l0, FaceBlocks& out, std::string& err) {
+  const int dim = m.dim, B = m.B, N = m.p + 1, nf = 2 * dim;
+  const int NF = dim == 2 ? N : N * N;
+  const int64_t n = m.ne;
+  out.NF = NF;
+  out.nf = nf;
+  out.diag.assign((size_t)n * B * B, 0.0);
+  out.R.assign((size_t)n * nf * NF * B, 0.0);
+  out.C.assign((size_t)n * nf * (B - NF) * NF, 0.0);
+  out.nbr.assign((size_t)n * nf, -1);
+  out.code.assign((size_t)n * nf, 0);
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(+ : bad)
+  for (int64_t u = 0; u < n; ++u) {
+    const int64_t e = l0.perm[u];
+    bool found = false;
+    for (int64_t j = l0.A.rowptr[u]; j < l0.A.rowptr[u + 1]; ++j)
+      if (l0.A.col[j] == u) {
+        std::memcpy(&out.diag[(size_t)u * B * B], &l0.A.val[(size_t)j * B * B], sizeof(double) * B * B);
+        found = true;
+      }
+    if (!found) bad += 1;
+    std::vector<char> on_fn(B);
+    for (int f = 0; f < nf; ++f) {
+      const int64_t rec = m.face_nbr[e * nf + f];
+      if (rec < 0) continue;
+      const int64_t nb = rec / nf;
+      const int fn = (int)(rec % nf);
+      out.nbr[u * nf + f] = (int32_t)l0.inv[nb];
+      out.code[u * nf + f] = (int8_t)fn;
+      const double* blk = &m.A.val[(size_t)(m.A.rowptr[e] + m.face_slot[e * nf + f]) * B * B];
+      double* R = &out.R[((size_t)u * nf + f) * NF * B];
+      double* C = &out.C[((size_t)u * nf + f) * (B - NF) * NF];
+      for (int r = 0; r < NF; ++r)
+        for (int c = 0; c < B; ++c) R[r * B + c] = blk[face_dof(dim, N, f, r) * B + c];
+      std::fill(on_fn.begin(), on_fn.end(), 0);
+      for (int jf = 0; jf < NF; ++jf) on_fn[face_dof(dim, N, fn, jf)] = 1;
+      for (int r = 0; r < B - NF; ++r) {
+        const int row = off_dof(dim, N, f, r);
+        for (int jf = 0; jf < NF; ++jf) C[r * NF + jf] = blk[row * B + face_dof(dim, N, fn, jf)];
+        for (int c = 0; c < B; ++c)
+          if (!on_fn[c] && blk[row * B + c] != 0.0) bad += 1;
+      }
+    }
+  }
+  if (bad) {
+    err = "the fine operator lacks the face structure of a GLL nodal basis";
+    return AGG_EINVAL;
   }
   return AGG_OK;
 }

@@ -101,6 +101,27 @@ def test_hierarchy_matches_oracle(case):
             assert np.all(np.diff(parent) >= 0)
 
 
+def test_coupling_blocks_have_exact_face_structure(case):
+    """A GLL nodal basis function whose node is off a face vanishes on it, so
+    the coupling block of two face neighbours is zero, exactly, outside
+    (e's rows on the face) x (all columns) and (all rows) x (n's columns on
+    its face). The face-structured device operator stores only those parts."""
+    wl, _, mesh = case
+    rp, cols, vals = mesh.stiffness_bsr()
+    d, B = wl.mesh.dim, mesh.B
+    N = round(B ** (1.0 / d))
+    idx = np.arange(B)
+    on = np.array([(idx // N ** (f // 2)) % N == (f % 2) * (N - 1) for f in range(2 * d)])
+    off_both = ~on[:, None, :, None] & ~on[None, :, None, :]          # [f, fn, row, col]
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    blocks = vals[cols != rows]
+    assert len(blocks) > 0
+    zero = np.all(np.where(off_both[None], blocks[:, None, None], 0.0) == 0.0, axis=(3, 4))
+    assert np.all(zero.any(axis=(1, 2)))
+    # and the structure is not vacuous: the parts themselves carry nonzeros
+    assert np.count_nonzero(blocks) > 0.3 * blocks.size * (1 - ((B - B // N) / B) ** 2)
+
+
 def test_bad_maps_are_rejected():
     wl = W.square_2d_fhn(8, 1)
     mesh = aggmg.Mesh.from_workload(wl)
