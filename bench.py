@@ -44,7 +44,9 @@ def parse():
                          "and hexahedra of p <= 2, assembled otherwise)")
     ap.add_argument("--workload", default="jsquare2d", choices=list(WORKLOADS))
     ap.add_argument("--n", type=int, default=None, help="elements per direction (box workloads)")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=None,
+                    help="steps of the end-to-end leg (default: --steps; it reruns the timed steps "
+                         "from the same state)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-kernel", type=int, default=None,
                     help="set up, launch kernel id K three times (for ncu) and exit")
@@ -215,6 +217,7 @@ def run_ours(args, rank, world):
     u = torch.zeros(N, dtype=torch.float64, device=dev)
     w = torch.zeros(N, dtype=torch.float64, device=dev)
     its_w = sim.step(u, w, args.warmup)                      # warm-up steps (stimulus on)
+    u_start, w_start = u.clone(), w.clone()                  # state at the timed region's start
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
@@ -234,9 +237,14 @@ def run_ours(args, rank, world):
         t = float(tt.item())
     total_steps = args.steps * world
     value = total_steps / t
-    # ---- end to end through the public API with pinned host state
-    uh = u.cpu().pin_memory()
-    wh = w.cpu().pin_memory()
+    # ---- end to end through the public API with pinned host state: the same
+    # time steps as the timed region, rerun from its starting state
+    if args.e2e_steps is None:
+        args.e2e_steps = args.steps
+    u_end = u.clone()
+    uh = u_start.cpu().pin_memory()
+    wh = w_start.cpu().pin_memory()
+    sim.set_clock(args.warmup)
     torch.cuda.synchronize()
     e0 = time.perf_counter()
     ev0.record(stream)
@@ -250,6 +258,9 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     t_e2e = ev0.elapsed_time(ev1) / 1e3
     del e0
+    e2e_same = None
+    if args.e2e_steps == args.steps:
+        e2e_same = bool(torch.equal(uh.to(dev), u_end))     # bitwise: deterministic reductions
     # ---- dominant kernel, timed live with events on the launching stream
     kid = 1
     reps = 50
@@ -308,7 +319,9 @@ def run_ours(args, rank, world):
         "iterations": {"mean": float(np.mean(its)), "min": int(min(its)), "max": int(max(its)),
                        "std": float(np.std(its)), "warmup": its_w},
         "e2e": {"value": args.e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * N * 8,
-                "d2h_bytes_per_step": 2 * N * 8},
+                "d2h_bytes_per_step": 2 * N * 8, "steps": args.e2e_steps,
+                "same_steps_as_timed": args.e2e_steps == args.steps,
+                "same_final_state_as_timed": e2e_same},
         "roofline": roof, "fine_fp64_spmv": other,
         "gpu_launches": launches,
         "clocks": clk.summary(),
