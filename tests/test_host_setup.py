@@ -10,6 +10,14 @@ from paper_2602_16312_gb300 import aggmg
 from paper_2602_16312_gb300 import workloads as W
 
 
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    """The host set-up runs in libaggmg.so: build it (nvcc cross-compiles
+    without a GPU) if this checkout has no current build."""
+    from paper_2602_16312_gb300 import build
+    build.build()
+
+
 def _bsr_to_csr(rp, cols, vals, n_rows, n_cols, perm=None):
     B = vals.shape[1]
     rows = np.repeat(np.arange(n_rows), np.diff(rp))
