@@ -194,6 +194,28 @@ class Engine : public EngineBase {
     return s;
   }
 
+  // smoother block inverses in the unit kernels' layout: packed upper
+  // triangle of the symmetrised block for B <= 32, full blocks otherwise
+  int upload_dinv(const std::vector<double>& blocks, int64_t n, int64_t nsl, TD** out, std::string& err) {
+    if constexpr (B > 32) {
+      return upload_blocks<TD>(blocks, n, nsl, out, err);
+    } else {
+      constexpr int KP = SymPad<TD, B>::KP, VW = Vec<TD>::W;
+      std::vector<TD> hv((size_t)nsl * SL * KP, to_storage<TD>(0.0));
+      for (int64_t u = 0; u < n; ++u) {
+        const double* m = &blocks[(size_t)u * B * B];
+        TD* sb = &hv[(size_t)(u / SL) * SL * KP];
+        const int lane = (int)(u % SL);
+        for (int j = 0; j < B; ++j)
+          for (int i = 0; i <= j; ++i) {
+            const int k = j * (j + 1) / 2 + i;
+            sb[((size_t)(k / VW) * SL + lane) * VW + (k % VW)] = to_storage<TD>(0.5 * (m[i * B + j] + m[j * B + i]));
+          }
+      }
+      return upload(out, hv.data(), hv.size(), err);
+    }
+  }
+
   // ROWS x COLS row-major block -> sliced column-major chunks (k = c ROWS + r)
   template <typename TS>
   static void pack_rect(const double* blk, TS* slot_base, int lane, int rows, int cols) {
@@ -487,7 +509,7 @@ class Engine : public EngineBase {
       if (!coarsest) {
         // level 0 keeps its slot structure only (its operator is face-structured)
         if ((rc = upload_sell<T>(hl.A, v.nsl, &v.slice_ptr, &v.cols, &v.vals, err, l > 0))) return rc;
-        if ((rc = upload_blocks<TD>(hl.Dinv, hl.n, v.nsl, &v.Dinv, err))) return rc;
+        if ((rc = upload_dinv(hl.Dinv, hl.n, v.nsl, &v.Dinv, err))) return rc;
         if ((rc = upload_blocks<T>(hl.P, hl.n, v.nsl, &v.P, err))) return rc;
         std::vector<int32_t> par(v.nsl * SL, 0);
         std::copy(hl.parent.begin(), hl.parent.end(), par.begin());
@@ -879,6 +901,7 @@ class Engine : public EngineBase {
   int kernel_cost(int id, double& bytes, double& flops) const override {
     const double n0 = (double)lev_[0].n, N = n0 * B, bb = (double)B * B;
     const double sT = sizeof(T), sD = sizeof(TD);
+    const double bd = (B <= 32) ? (double)SymPad<TD, B>::NP : bb;   // stored smoother entries
     // face-structured operator: its stored entries and, per face slot, a
     // neighbour id and a face code
     const double fidx = n0 * 2 * FaceShape<B>::D * 5.0;
@@ -886,7 +909,7 @@ class Engine : public EngineBase {
     switch (id) {
       case 0: bytes = fe * 8 + fidx + 2 * N * 8; flops = 2 * fe; break;
       case 1:
-        bytes = (use_mf0() ? (double)mf_bytes_ : fe * sT + fidx) + n0 * bb * sD + 5 * N * sT;
+        bytes = (use_mf0() ? (double)mf_bytes_ : fe * sT + fidx) + n0 * bd * sD + 5 * N * sT;
         flops = 2 * fe + 2 * n0 * bb + 4 * N;
         break;
       case 2:

@@ -176,6 +176,38 @@ __device__ __forceinline__ void block_mtv_out(const TS* base, int lane, const A*
   }
 }
 
+// Symmetric B x B blocks (the smoother's block inverses, B <= 32) keep their
+// upper triangle only, column by column: entry (i, j), i <= j, at
+// k = j (j + 1) / 2 + i, in the same sliced chunk layout.
+template <typename TS, int B> struct SymPad {
+  static constexpr int VW = Vec<TS>::W;
+  static constexpr int NP = B * (B + 1) / 2;
+  static constexpr int KP = ((NP + VW - 1) / VW) * VW;
+};
+// Storage of the smoother blocks seen by the unit kernels: packed symmetric
+// for B <= 32, full for larger blocks (their column loop needs full columns).
+template <typename TS, int B> struct DinvPad {
+  static constexpr int KP = (B <= 32) ? SymPad<TS, B>::KP : Pad<TS, B>::KP;
+};
+
+// acc += M x for one packed symmetric sliced block (x a register array)
+template <typename TS, typename A, int B>
+__device__ __forceinline__ void sym_block_mv(const TS* base, int lane, const A* x, A* acc) {
+  constexpr int VW = ChunkLoad<TS, A>::VW;
+  A v[VW];
+#pragma unroll
+  for (int j = 0; j < B; ++j) {
+#pragma unroll
+    for (int i = 0; i <= j; ++i) {
+      const int k = j * (j + 1) / 2 + i;
+      if (k % VW == 0) ChunkLoad<TS, A>::load(base, k / VW, lane, v);
+      const A m = v[k % VW];
+      acc[i] += m * x[j];
+      if (i != j) acc[j] += m * x[i];
+    }
+  }
+}
+
 // Unit kernels: one warp per slice of 32 units; the grid covers every slice.
 template <int NTB>
 __device__ __forceinline__ int64_t first_slice() {
@@ -333,7 +365,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value, OpMinBlocks<Op>:
            T* __restrict__ x_new, T* __restrict__ d, T c1, T c2, int64_t nslices, const CGState* st) {
   constexpr int NTB = UnitThreads<B>::value;
   if (st && st->done) return;
-  constexpr int KPD = Pad<TD, B>::KP;
+  constexpr int KPD = DinvPad<TD, B>::KP;
   const int lane = threadIdx.x & 31;
   {
   const int64_t slice = first_slice<NTB>();
@@ -373,7 +405,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value, OpMinBlocks<Op>:
 #pragma unroll
       for (int r = 0; r < B; ++r) t[r] = rhs[o + r] - acc[r];
     }
-    block_mv<TD, T, B>(Db, lane, t, s);
+    sym_block_mv<TD, T, B>(Db, lane, t, s);
   }
 #pragma unroll
   for (int r = 0; r < B; ++r) {
