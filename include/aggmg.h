@@ -5,7 +5,8 @@
  *
  * The method (arXiv 2602.16312):
  *   - monodomain model and ionic models: Section 2 (Eq. monodomain, the
- *     FitzHugh-Nagumo model of Section 2.3.1);
+ *     FitzHugh-Nagumo model of Section 2.3.1, the Bueno-Orovio model of
+ *     Section 2.3.2, Eq. BuenoOrovio);
  *   - SIPG forms a_h, m_h and penalty: Section 3; linear system
  *     A0 u^{n+1} = b with A0 = c M + A: Eq. fully_discrete;
  *   - nested agglomerated levels, inherited operators
@@ -202,17 +203,45 @@ agg_status agg_operator_apply_static(agg_hier_t hier, int level, const double* x
                                      void* stream);
 
 /* ------------------------------------------------------------------ ionic models */
-typedef enum { AGG_FHN = 0, AGG_ALIEV_PANFILOV = 1 } agg_ionic_model;
+typedef enum { AGG_FHN = 0, AGG_ALIEV_PANFILOV = 1, AGG_BUENO_OROVIO = 2 } agg_ionic_model;
+
+/* Bueno-Orovio (Section 2.3.2, Eq. BuenoOrovio; values in the paper's
+ * appendix table). Names follow the paper: tau1p = tau_1', tau1pp = tau_1'',
+ * tau1plus = tau_1^+, tau2inf = tau_2^inf, tauo_p = tau_o', tauso_pp =
+ * tau_so'', winf_star = w_inf^*, V1m = V_1^-, Vhat = V^, and so on; uo is the
+ * reference potential of the I_so drift term (u - uo). With H_z0 the unit
+ * step at z0 (1 for u >= z0) and H^k_z0 = (1 + tanh(k (u - z0)))/2, three
+ * gates evolve as dw_i/dt = (b_i - a_i) w_i + a_i w_i^inf:
+ *   a0 = (1 - H_V1)/(H_V1m (tau1pp - tau1p) + tau1p), b0 = -H_V1/tau1plus,
+ *   w0^inf = 1 - H_V1m;
+ *   a1 = (1 - H_V2)/(H^k2_V2m (tau2pp - tau2p) + tau2p), b1 = -H_V2/tau2plus,
+ *   w1^inf = H_Vo (winf_star - 1 + u/tau2inf) + 1 - u/tau2inf;
+ *   a2 = 1/(H_V2 (tau3pp - tau3p) + tau3p), b2 = 0, w2^inf = H^k3_V3;
+ * and I_ion = -H_V1 (u - V1)(Vhat - u) w0/taufi
+ *           + (1 - H_V2)(u - uo)/(H_Vo (tauo_pp - tauo_p) + tauo_p)
+ *           + H_V2/(H^kso_Vso (tauso_pp - tauso_p) + tauso_p) - H_V2 w1 w2/tausi. */
+typedef struct {
+  double tau1p, tau1pp, tau1plus, tau2p, tau2pp, tau2plus, tau2inf, tau3p, tau3pp;
+  double taufi, tauo_p, tauo_pp, tauso_p, tauso_pp, tausi;
+  double k2, k3, kso, winf_star;
+  double V1, V1m, V2, V2m, V3, Vhat, Vo, Vso, uo;
+} agg_bueno_orovio_params;
 
 /* FitzHugh-Nagumo (Section 2.3.1): I = k u (u-a)(u-1) + w, H = eps (u - gamma w).
  * Aliev-Panfilov (not in the paper; published 1996 form):
- *   I = k u (u-a)(u-1) + u w, H = (eps + mu1 w/(u+mu2)) (-w - k u (u-a-1)). */
+ *   I = k u (u-a)(u-1) + u w, H = (eps + mu1 w/(u+mu2)) (-w - k u (u-a-1)).
+ * Bueno-Orovio: the fields of `bo` (k ... mu2 unused).
+ * Gating state: FitzHugh-Nagumo and Aliev-Panfilov have one gate per DoF,
+ * Bueno-Orovio three; an array w of n DoFs holds the gates one after the
+ * other, w[g * n + i] (gate g of DoF i). */
 typedef struct {
   int model;
   double k, a, eps, gamma, mu1, mu2;
+  agg_bueno_orovio_params bo;
 } agg_ionic_params;
 
-/* w <- w + dt H(u, w) at n DoFs (forward Euler; Section 3.1, first bullet). */
+/* w <- w + dt H(u, w) at n DoFs (forward Euler; Section 3.1, first bullet).
+ * w_dev holds n_gates * n values (gate-major, see above). */
 agg_status agg_ionic_update(const agg_ionic_params* prm, double dt, int64_t n, const double* u_dev,
                             double* w_dev, void* stream);
 
@@ -241,7 +270,8 @@ typedef struct {
  *   w^{-1} = w - dt H(u, w).
  * Both: A0 u^{n+1} = b by PCG warm-started from u^n. */
 agg_status agg_monodomain_create(agg_hier_t hier, const agg_sim_opts* opts, agg_sim_t* out);
-/* Advances n_steps steps in place on u_dev, w_dev ([n_dofs] each); the
+/* Advances n_steps steps in place on u_dev ([n_dofs]) and w_dev
+ * ([n_gates][n_dofs], gate-major as for agg_ionic_update); the
  * stimulus clock is the handle's step counter (starts at 0). iters_out: host
  * array of n_steps PCG iteration counts, or NULL. Synchronises `stream`. */
 agg_status agg_monodomain_step(agg_sim_t sim, int n_steps, double* u_dev, double* w_dev,
@@ -259,8 +289,9 @@ agg_status agg_monodomain_set_clock(agg_sim_t sim, int64_t step);
  * grad_logD_dev [n_elements] accumulates, per element e, the derivative of L
  * with respect to log s_e for D_e -> s_e D_e: -lambda^T A_e u^{n+1}, A_e the
  * part of A built with D_e (element-local volume form and e's share of its
- * face forms). Needs a mesh created with adjoint_data = 1. Synchronises
- * `stream`; returns the adjoint solve's status. */
+ * face forms). Needs a mesh created with adjoint_data = 1 and a one-gate
+ * ionic model (AGG_EUNSUPPORTED for Bueno-Orovio). Synchronises `stream`;
+ * returns the adjoint solve's status. */
 agg_status agg_monodomain_adjoint_step(agg_sim_t sim, const double* u_n_dev, const double* w_n_dev,
                                        const double* u_np1_dev, double* ubar_dev, double* wbar_dev,
                                        double* grad_logD_dev, void* stream);

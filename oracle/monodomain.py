@@ -40,6 +40,29 @@ published form (Aliev & Panfilov 1996) is used:
   H     = (eps + mu1 w / (u + mu2)) (-w - k u (u - a - 1)).
 Parity of these constants is unpinned by the paper (chosen readings); the
 pins are the model equilibria and the space-clamped recurrence.
+
+Bueno-Orovio (Section 2.3.2, Eq. BuenoOrovio; model 2): three gates
+w = (w0, w1, w2), each dw_i/dt = (b_i - a_i) w_i + a_i w_i^inf, with
+H_z0(z) the unit step at z0 (1 for z >= z0) and H^k_z0(z) = (1 + tanh(k (z - z0)))/2:
+  a0 = (1 - H_V1) / (H_V1m (tau1'' - tau1') + tau1'),   b0 = -H_V1 / tau1+,
+  w0^inf = 1 - H_V1m,
+  a1 = (1 - H_V2) / (H^k2_V2m (tau2'' - tau2') + tau2'), b1 = -H_V2 / tau2+,
+  w1^inf = H_Vo (w*inf - 1 + u / tau2inf) + 1 - u / tau2inf,
+  a2 = 1 / (H_V2 (tau3'' - tau3') + tau3'),              b2 = 0,
+  w2^inf = H^k3_V3,
+  I_ion = I_fi + I_so + I_si,
+  I_fi = -H_V1 (u - V1)(Vhat - u) w0 / tau_fi,
+  I_so = (1 - H_V2)(u - uo) / (H_Vo (tau_o'' - tau_o') + tau_o')
+         + H_V2 / (H^kso_Vso (tau_so'' - tau_so') + tau_so'),
+  I_si = -H_V2 w1 w2 / tau_si.
+Readings: the superscript "-" of H in a0 and w0^inf is the threshold V1m
+(V1^- in the text), the one of H in a1 is the smoothed step at V2m with
+slope k2; w2^inf uses V3 with slope k3; the paper prints (u - V_o) in I_so,
+but with it the resting state u = 0, w = (1, 1, H^k3_V3(0)) carries the
+current -V_o / tau_o' = -1 and is not an equilibrium, so the model's
+reference potential uo = 0 is used (tests pin the equilibrium). Parameter
+values: the appendix table with its repeated rows taken once. The adjoint
+is built for models 0 and 1 only.
 """
 from dataclasses import dataclass
 
@@ -47,11 +70,46 @@ import numpy as np
 
 from .multigrid import pcg, vcycle
 
-FHN, ALIEV_PANFILOV = 0, 1
+FHN, ALIEV_PANFILOV, BUENO_OROVIO = 0, 1, 2
+
+
+def _step(z, z0):
+    """Unit step at z0: 1 where z >= z0."""
+    return (np.asarray(z) >= z0).astype(float)
+
+
+def _smooth_step(z, z0, k):
+    return 0.5 * (1.0 + np.tanh(k * (np.asarray(z) - z0)))
+
+
+def bueno_orovio(p, u, w):
+    """(I_ion, H) of the Bueno-Orovio model; w has one row per gate (3, n)."""
+    w0, w1, w2 = w[0], w[1], w[2]
+    H_V1, H_V1m = _step(u, p["V1"]), _step(u, p["V1m"])
+    H_V2, H_Vo = _step(u, p["V2"]), _step(u, p["Vo"])
+    a0 = (1.0 - H_V1) / (H_V1m * (p["tau1pp"] - p["tau1p"]) + p["tau1p"])
+    b0 = -H_V1 / p["tau1plus"]
+    w0_inf = 1.0 - H_V1m
+    a1 = (1.0 - H_V2) / (_smooth_step(u, p["V2m"], p["k2"]) * (p["tau2pp"] - p["tau2p"]) + p["tau2p"])
+    b1 = -H_V2 / p["tau2plus"]
+    w1_inf = H_Vo * (p["winf_star"] - 1.0 + u / p["tau2inf"]) + 1.0 - u / p["tau2inf"]
+    a2 = 1.0 / (H_V2 * (p["tau3pp"] - p["tau3p"]) + p["tau3p"])
+    w2_inf = _smooth_step(u, p["V3"], p["k3"])
+    H = np.stack([(b0 - a0) * w0 + a0 * w0_inf,
+                  (b1 - a1) * w1 + a1 * w1_inf,
+                  -a2 * w2 + a2 * w2_inf])
+    I_fi = -H_V1 * (u - p["V1"]) * (p["Vhat"] - u) * w0 / p["taufi"]
+    I_so = ((1.0 - H_V2) * (u - p["uo"]) / (H_Vo * (p["tauo_pp"] - p["tauo_p"]) + p["tauo_p"])
+            + H_V2 / (_smooth_step(u, p["Vso"], p["kso"]) * (p["tauso_pp"] - p["tauso_p"]) + p["tauso_p"]))
+    I_si = -H_V2 * w1 * w2 / p["tausi"]
+    return I_fi + I_so + I_si, H
 
 
 def ionic(prm, u, w):
-    """(I_ion(u, w), H(u, w)) of the model in prm (dict as in workloads)."""
+    """(I_ion(u, w), H(u, w)) of the model in prm (dict as in workloads).
+    Models 0, 1: w and H have the shape of u; model 2: one row per gate."""
+    if prm["model"] == BUENO_OROVIO:
+        return bueno_orovio(prm, u, w)
     k, a, eps = prm["k"], prm["a"], prm["eps"]
     if prm["model"] == FHN:
         I = k * u * (u - a) * (u - 1.0) + w
@@ -64,7 +122,10 @@ def ionic(prm, u, w):
 
 
 def ionic_jacobian(prm, u, w):
-    """Partial derivatives (I_u, I_w, H_u, H_w) of the model, pointwise."""
+    """Partial derivatives (I_u, I_w, H_u, H_w) of the model, pointwise
+    (models 0 and 1)."""
+    if prm["model"] == BUENO_OROVIO:
+        raise NotImplementedError("the adjoint is built for the one-gate models")
     k, a, eps = prm["k"], prm["a"], prm["eps"]
     dI_du = k * (3.0 * u * u - 2.0 * (a + 1.0) * u + a)
     if prm["model"] == FHN:

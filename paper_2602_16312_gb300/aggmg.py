@@ -19,7 +19,7 @@ AGG_OK, AGG_EINVAL, AGG_ENOMEM, AGG_ECUDA, AGG_ENOTSPD, AGG_ENOTCONV, AGG_ENAN, 
     0, -1, -2, -3, -4, -5, -6, -7)
 AGG_F64, AGG_F32, AGG_F32_BF16SMOOTH = 0, 1, 2
 PRECISIONS = {"f64": AGG_F64, "f32": AGG_F32, "bf16s": AGG_F32_BF16SMOOTH}
-AGG_FHN, AGG_ALIEV_PANFILOV = 0, 1
+AGG_FHN, AGG_ALIEV_PANFILOV, AGG_BUENO_OROVIO = 0, 1, 2
 
 
 class AggError(RuntimeError):
@@ -50,9 +50,18 @@ class PCGResult(C.Structure):
     _fields_ = [("iterations", C.c_int), ("r0_norm", C.c_double), ("r_norm", C.c_double), ("status", C.c_int)]
 
 
+BO_FIELDS = ("tau1p", "tau1pp", "tau1plus", "tau2p", "tau2pp", "tau2plus", "tau2inf", "tau3p", "tau3pp",
+             "taufi", "tauo_p", "tauo_pp", "tauso_p", "tauso_pp", "tausi", "k2", "k3", "kso", "winf_star",
+             "V1", "V1m", "V2", "V2m", "V3", "Vhat", "Vo", "Vso", "uo")
+
+
+class BuenoOrovioParams(C.Structure):
+    _fields_ = [(f, C.c_double) for f in BO_FIELDS]
+
+
 class IonicParams(C.Structure):
     _fields_ = [("model", C.c_int), ("k", C.c_double), ("a", C.c_double), ("eps", C.c_double),
-                ("gamma", C.c_double), ("mu1", C.c_double), ("mu2", C.c_double)]
+                ("gamma", C.c_double), ("mu1", C.c_double), ("mu2", C.c_double), ("bo", BuenoOrovioParams)]
 
 
 class SimOpts(C.Structure):
@@ -358,12 +367,22 @@ class Hierarchy:
             pass
 
 
+def n_gates(d: dict) -> int:
+    """Gating variables per DoF of the model (w holds n_gates rows of n DoFs)."""
+    return 3 if int(d["model"]) == AGG_BUENO_OROVIO else 1
+
+
 def ionic_params(d: dict) -> IonicParams:
-    return IonicParams(int(d["model"]), d["k"], d["a"], d["eps"], d.get("gamma", 0.0), d.get("mu1", 0.0),
-                       d.get("mu2", 0.0))
+    bo = BuenoOrovioParams(*[d[f] for f in BO_FIELDS]) if int(d["model"]) == AGG_BUENO_OROVIO \
+        else BuenoOrovioParams()
+    return IonicParams(int(d["model"]), d.get("k", 0.0), d.get("a", 0.0), d.get("eps", 0.0), d.get("gamma", 0.0),
+                       d.get("mu1", 0.0), d.get("mu2", 0.0), bo)
 
 
 def ionic_update(prm: dict, dt: float, u, w, stream=None):
+    """agg_ionic_update; w holds n_gates(prm) gate rows of u.numel() values."""
+    if w.numel() != n_gates(prm) * u.numel():
+        raise ValueError("w must hold n_gates * n values")
     p = ionic_params(prm)
     _check(lib().agg_ionic_update(C.byref(p), dt, u.numel(), C.c_void_p(_dptr(u)), C.c_void_p(_dptr(w)),
                                   C.c_void_p(_stream(stream))))
@@ -381,8 +400,12 @@ class Monodomain:
         _check(lib().agg_monodomain_create(hier.handle, C.byref(o), C.byref(h)))
         self.handle = h
         self.hier = hier
+        self.n_gates = n_gates(ionic)
 
     def step(self, u, w, n_steps=1, stream=None, iters=True):
+        """Advance in place; w holds n_gates rows of u.numel() gate values."""
+        if w.numel() != self.n_gates * u.numel():
+            raise ValueError("w must hold n_gates * n_dofs values")
         its = (C.c_int * n_steps)() if iters else None
         _check(lib().agg_monodomain_step(self.handle, n_steps, C.c_void_p(_dptr(u)), C.c_void_p(_dptr(w)),
                                          its, C.c_void_p(_stream(stream))))

@@ -392,9 +392,9 @@ agg_status agg_ionic_update(const agg_ionic_params* p, double dt, int64_t n, con
                             void* stream) {
   if (!p || (n > 0 && (!u || !w))) return fail(AGG_EINVAL, "NULL argument");
   if (n < 0) return fail(AGG_EINVAL, "n < 0");
-  if (p->model != AGG_FHN && p->model != AGG_ALIEV_PANFILOV) return fail(AGG_EINVAL, "ionic model");
+  if (p->model < AGG_FHN || p->model > AGG_BUENO_OROVIO) return fail(AGG_EINVAL, "ionic model");
   if (n == 0) return AGG_OK;
-  IonicParams ip{p->model, p->k, p->a, p->eps, p->gamma, p->mu1, p->mu2};
+  IonicParams ip{p->model, p->k, p->a, p->eps, p->gamma, p->mu1, p->mu2, p->bo};
   const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
   k_ionic_update<<<blocks, 256, 0, (cudaStream_t)stream>>>(ip, dt, n, u, w);
   cudaError_t e = cudaGetLastError();
@@ -414,7 +414,7 @@ agg_status agg_monodomain_create(agg_hier_t h, const agg_sim_opts* o, agg_sim_t*
   if (std::fabs(c - h->mass_coeff) > 1e-12 * std::fabs(c))
     return fail(AGG_EINVAL, o->scheme == 1 ? "hierarchy mass_coeff differs from 3 chi_m c_m / (2 dt)"
                                            : "hierarchy mass_coeff differs from chi_m c_m / dt");
-  if (o->ionic.model != AGG_FHN && o->ionic.model != AGG_ALIEV_PANFILOV) return fail(AGG_EINVAL, "ionic model");
+  if (o->ionic.model < AGG_FHN || o->ionic.model > AGG_BUENO_OROVIO) return fail(AGG_EINVAL, "ionic model");
   SimParams sp;
   sp.model = o->ionic.model;
   sp.k = o->ionic.k;
@@ -423,6 +423,7 @@ agg_status agg_monodomain_create(agg_hier_t h, const agg_sim_opts* o, agg_sim_t*
   sp.gamma = o->ionic.gamma;
   sp.mu1 = o->ionic.mu1;
   sp.mu2 = o->ionic.mu2;
+  sp.bo = o->ionic.bo;
   sp.dt = o->dt;
   sp.chi = o->chi_m;
   sp.cm = o->c_m;

@@ -4,6 +4,7 @@
 // Dot products are reduced deterministically: a fixed grid writes one partial
 // per block and the last block to finish sums them in block order.
 #pragma once
+#include "../../include/aggmg.h"
 #include "kernels.cuh"
 
 namespace aggmg {
@@ -194,25 +195,74 @@ static __global__ void k_scatter_units(const TI* __restrict__ src, TO* __restric
 struct IonicParams {
   int model;
   double k, a, eps, gamma, mu1, mu2;
+  agg_bueno_orovio_params bo;
 };
 
-__device__ __forceinline__ void ionic_eval(const IonicParams& p, double u, double w, double& I, double& H) {
+// Gates per DoF: FitzHugh-Nagumo and Aliev-Panfilov 1, Bueno-Orovio 3; gate g
+// of DoF i lives at w[g * stride + i].
+constexpr int kMaxGates = 3;
+__host__ __device__ inline int ionic_gates(int model) { return model == 2 ? 3 : 1; }
+
+__device__ __forceinline__ double unit_step(double z, double z0) { return z >= z0 ? 1.0 : 0.0; }
+__device__ __forceinline__ double smooth_step(double z, double z0, double k) {
+  return 0.5 * (1.0 + tanh(k * (z - z0)));
+}
+
+// Bueno-Orovio (Section 2.3.2, Eq. BuenoOrovio): I_ion and the three gate rates
+__device__ __forceinline__ void bueno_orovio_eval(const agg_bueno_orovio_params& p, double u, const double* w,
+                                                  double& I, double* H) {
+  const double hv1 = unit_step(u, p.V1), hv1m = unit_step(u, p.V1m);
+  const double hv2 = unit_step(u, p.V2), hvo = unit_step(u, p.Vo);
+  const double a0 = (1.0 - hv1) / (hv1m * (p.tau1pp - p.tau1p) + p.tau1p);
+  const double b0 = -hv1 / p.tau1plus;
+  const double w0inf = 1.0 - hv1m;
+  const double a1 = (1.0 - hv2) / (smooth_step(u, p.V2m, p.k2) * (p.tau2pp - p.tau2p) + p.tau2p);
+  const double b1 = -hv2 / p.tau2plus;
+  const double w1inf = hvo * (p.winf_star - 1.0 + u / p.tau2inf) + 1.0 - u / p.tau2inf;
+  const double a2 = 1.0 / (hv2 * (p.tau3pp - p.tau3p) + p.tau3p);
+  const double w2inf = smooth_step(u, p.V3, p.k3);
+  H[0] = (b0 - a0) * w[0] + a0 * w0inf;
+  H[1] = (b1 - a1) * w[1] + a1 * w1inf;
+  H[2] = -a2 * w[2] + a2 * w2inf;
+  const double ifi = -hv1 * (u - p.V1) * (p.Vhat - u) * w[0] / p.taufi;
+  const double iso = (1.0 - hv2) * (u - p.uo) / (hvo * (p.tauo_pp - p.tauo_p) + p.tauo_p) +
+                     hv2 / (smooth_step(u, p.Vso, p.kso) * (p.tauso_pp - p.tauso_p) + p.tauso_p);
+  const double isi = -hv2 * w[1] * w[2] / p.tausi;
+  I = ifi + iso + isi;
+}
+
+// I_ion(u, w) and the gate rates H(u, w) (w, H: ionic_gates(model) values)
+__device__ __forceinline__ void ionic_eval(const IonicParams& p, double u, const double* w, double& I, double* H) {
+  if (p.model == 2) {
+    bueno_orovio_eval(p.bo, u, w, I, H);
+    return;
+  }
   const double cub = p.k * u * (u - p.a) * (u - 1.0);
   if (p.model == 0) {
-    I = cub + w;
-    H = p.eps * (u - p.gamma * w);
+    I = cub + w[0];
+    H[0] = p.eps * (u - p.gamma * w[0]);
   } else {
-    I = cub + u * w;
-    H = (p.eps + p.mu1 * w / (u + p.mu2)) * (-w - p.k * u * (u - p.a - 1.0));
+    I = cub + u * w[0];
+    H[0] = (p.eps + p.mu1 * w[0] / (u + p.mu2)) * (-w[0] - p.k * u * (u - p.a - 1.0));
   }
+}
+
+// gate values of DoF i (stride between gates) into g[]
+__device__ __forceinline__ void load_gates(const double* w, int64_t stride, int64_t i, int ng, double* g) {
+#pragma unroll
+  for (int k = 0; k < kMaxGates; ++k) g[k] = (k < ng) ? w[k * stride + i] : 0.0;
 }
 
 static __global__ void k_ionic_update(IonicParams prm, double dt, int64_t n, const double* __restrict__ u,
                                double* __restrict__ w) {
+  const int ng = ionic_gates(prm.model);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double I, H;
-    ionic_eval(prm, u[i], w[i], I, H);
-    w[i] = w[i] + dt * H;
+    double g[kMaxGates], H[kMaxGates], I;
+    load_gates(w, n, i, ng, g);
+    ionic_eval(prm, u[i], g, I, H);
+#pragma unroll
+    for (int k = 0; k < kMaxGates; ++k)
+      if (k < ng) w[k * n + i] = g[k] + dt * H[k];
   }
 }
 
@@ -223,7 +273,8 @@ template <int B>
 static __global__ void __launch_bounds__(UnitThreads<B>::value)
     k_ionic_rhs(const double* __restrict__ Me, const double* __restrict__ u, double* __restrict__ w,
                 const double* __restrict__ mask, double* __restrict__ b, IonicParams prm, double dt, double chi,
-                double c, double iapp_value, int64_t iapp_steps, const int64_t* __restrict__ step, int64_t nslices) {
+                double c, double iapp_value, int64_t iapp_steps, const int64_t* __restrict__ step, int64_t nslices,
+                int64_t wstride) {
   constexpr int NTB = UnitThreads<B>::value;
   constexpr int KP = Pad<double, B>::KP;
   const int lane = threadIdx.x & 31;
@@ -234,13 +285,18 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
   const size_t o = (size_t)unit * B;
   const double ia = (*step < iapp_steps) ? iapp_value : 0.0;
   // per DoF: ionic update and the nodal load c u + I_app mask - chi I(u, w_new)
+  const int ng = ionic_gates(prm.model);
   auto nodal = [&](int r) {
     const double ur = u[o + r];
-    double I, H;
-    ionic_eval(prm, ur, w[o + r], I, H);
-    const double wn = w[o + r] + dt * H;
-    w[o + r] = wn;
-    ionic_eval(prm, ur, wn, I, H);
+    double g[kMaxGates], H[kMaxGates], I;
+    load_gates(w, wstride, o + r, ng, g);
+    ionic_eval(prm, ur, g, I, H);
+#pragma unroll
+    for (int k = 0; k < kMaxGates; ++k) {
+      g[k] += dt * H[k];
+      if (k < ng) w[k * wstride + o + r] = g[k];
+    }
+    ionic_eval(prm, ur, g, I, H);
     return c * ur + ia * mask[o + r] - chi * I;
   };
   double acc[B];
@@ -272,7 +328,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
     k_bdf2_start(const double* __restrict__ Minv, const double* __restrict__ A0u, const double* __restrict__ u,
                  const double* __restrict__ w, const double* __restrict__ mask, double* __restrict__ up,
                  double* __restrict__ wp, IonicParams prm, double dt, double chi, double cm, double c, double ia,
-                 int64_t nslices) {
+                 int64_t nslices, int64_t wstride) {
   constexpr int NTB = UnitThreads<B>::value;
   constexpr int KP = Pad<double, B>::KP;
   const int lane = threadIdx.x & 31;
@@ -284,14 +340,18 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
   for (int r = 0; r < B; ++r) t[r] = 0.0;
   block_mv<double, double, B>(Minv + (size_t)slice * SL * KP, lane, A0u + o, t);
 #pragma unroll
+  const int ng = ionic_gates(prm.model);
   for (int r = 0; r < B; ++r) {
-    const double ur = u[o + r], wr = w[o + r];
-    double I, H;
-    ionic_eval(prm, ur, wr, I, H);
+    const double ur = u[o + r];
+    double g[kMaxGates], H[kMaxGates], I;
+    load_gates(w, wstride, o + r, ng, g);
+    ionic_eval(prm, ur, g, I, H);
     const double f0 = ia * mask[o + r] - chi * I;
     const double udot = (f0 - (t[r] - c * ur)) / (chi * cm);
     up[o + r] = ur - dt * udot;
-    wp[o + r] = wr - dt * H;
+#pragma unroll
+    for (int k = 0; k < kMaxGates; ++k)
+      if (k < ng) wp[k * wstride + o + r] = g[k] - dt * H[k];
   }
 }
 
@@ -304,7 +364,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
     k_ionic_rhs_bdf2(const double* __restrict__ Me, const double* __restrict__ u, double* __restrict__ up,
                      double* __restrict__ w, double* __restrict__ wp, const double* __restrict__ mask,
                      double* __restrict__ b, IonicParams prm, double dt, double chi, double cm, double iapp_value,
-                     int64_t iapp_steps, const int64_t* __restrict__ step, int64_t nslices) {
+                     int64_t iapp_steps, const int64_t* __restrict__ step, int64_t nslices, int64_t wstride) {
   constexpr int NTB = UnitThreads<B>::value;
   constexpr int KP = Pad<double, B>::KP;
   const int lane = threadIdx.x & 31;
@@ -312,16 +372,26 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
   if (slice >= nslices) return;
   const size_t o = (size_t)(slice * SL + lane) * B;
   const double ia = (*step < iapp_steps) ? iapp_value : 0.0;
+  const int ng = ionic_gates(prm.model);
   auto nodal = [&](int r) {
-    const double un = u[o + r], upr = up[o + r], wn = w[o + r], wpr = wp[o + r];
-    const double us = 2.0 * un - upr, ws = 2.0 * wn - wpr;
-    double I, H;
+    const double un = u[o + r], upr = up[o + r];
+    const double us = 2.0 * un - upr;
+    double wn[kMaxGates], wpr[kMaxGates], ws[kMaxGates], w1[kMaxGates], H[kMaxGates], I;
+    load_gates(w, wstride, o + r, ng, wn);
+    load_gates(wp, wstride, o + r, ng, wpr);
+#pragma unroll
+    for (int k = 0; k < kMaxGates; ++k) ws[k] = 2.0 * wn[k] - wpr[k];
     ionic_eval(prm, us, ws, I, H);
-    const double w1 = (4.0 * wn - wpr) / 3.0 + (2.0 * dt / 3.0) * H;
+#pragma unroll
+    for (int k = 0; k < kMaxGates; ++k) w1[k] = (4.0 * wn[k] - wpr[k]) / 3.0 + (2.0 * dt / 3.0) * H[k];
     ionic_eval(prm, us, w1, I, H);
     up[o + r] = un;
-    wp[o + r] = wn;
-    w[o + r] = w1;
+#pragma unroll
+    for (int k = 0; k < kMaxGates; ++k)
+      if (k < ng) {
+        wp[k * wstride + o + r] = wn[k];
+        w[k * wstride + o + r] = w1[k];
+      }
     return chi * cm / (2.0 * dt) * (4.0 * un - upr) + ia * mask[o + r] - chi * I;
   };
   double acc[B];
@@ -398,9 +468,10 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
 #pragma unroll
   for (int r = 0; r < B; ++r) {
     const double un = u_n[o + r], wn = w_n[o + r];
-    double I, H, Iu, Iw, Hu, Hw, Iu1, Iw1, Hu1, Hw1;
-    ionic_eval(prm, un, wn, I, H);
-    const double w1 = wn + dt * H;
+    double I, H[kMaxGates], Iu, Iw, Hu, Hw, Iu1, Iw1, Hu1, Hw1;
+    const double wg[kMaxGates] = {wn, 0.0, 0.0};
+    ionic_eval(prm, un, wg, I, H);                 // one-gate models only
+    const double w1 = wn + dt * H[0];
     ionic_jac(prm, un, w1, Iu1, Iw1, Hu1, Hw1);
     ionic_jac(prm, un, wn, Iu, Iw, Hu, Hw);
     const double wt = wbar[o + r] - chi * Iw1 * q[r];

@@ -6,6 +6,7 @@
 
 #include <string>
 
+#include "../../include/aggmg.h"
 #include "setup.h"
 
 namespace aggmg {
@@ -23,6 +24,7 @@ struct SolveResult {
 struct SimParams {
   int model = 0;
   double k = 0, a = 0, eps = 0, gamma = 0, mu1 = 0, mu2 = 0;
+  agg_bueno_orovio_params bo{};
   double dt = 0, chi = 1, cm = 1;
   double iapp_value = 0;
   int64_t iapp_steps = 0;

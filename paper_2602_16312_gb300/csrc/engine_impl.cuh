@@ -385,16 +385,16 @@ class Engine : public EngineBase {
   }
 
   void launch_step_prologue(cudaStream_t s) {
-    IonicParams ip{sp_.model, sp_.k, sp_.a, sp_.eps, sp_.gamma, sp_.mu1, sp_.mu2};
+    IonicParams ip{sp_.model, sp_.k, sp_.a, sp_.eps, sp_.gamma, sp_.mu1, sp_.mu2, sp_.bo};
     if (sp_.scheme == 1) {
       k_ionic_rhs_bdf2<B><<<bgrid(0, lev_[0].nsl), NTB, 0, s>>>(Me_, x_, up_, w_, wp_, mask_, b_, ip, sp_.dt, sp_.chi,
                                                               sp_.cm, sp_.iapp_value, sp_.iapp_steps, step_,
-                                                              lev_[0].nsl);
+                                                              lev_[0].nsl, N0());
       return;
     }
     const double c = sp_.chi * sp_.cm / sp_.dt;
-    k_ionic_rhs<B><<<bgrid(k_ionic_rhs<B>, lev_[0].nsl), NTB, 0, s>>>(Me_, x_, w_, mask_, b_, ip, sp_.dt, sp_.chi, c, sp_.iapp_value,
-                                       sp_.iapp_steps, step_, lev_[0].nsl);
+    k_ionic_rhs<B><<<bgrid(0, lev_[0].nsl), NTB, 0, s>>>(Me_, x_, w_, mask_, b_, ip, sp_.dt, sp_.chi, c,
+                                                         sp_.iapp_value, sp_.iapp_steps, step_, lev_[0].nsl, N0());
   }
 
   // Builds [prologue] -> WHILE(body) -> [epilogue]; prologue/epilogue are
@@ -781,7 +781,7 @@ class Engine : public EngineBase {
     int rc;
     const int64_t N = N0();
     if (!w_) {
-      if ((rc = dalloc(&w_, N, err))) return rc;
+      if ((rc = dalloc(&w_, kMaxGates * N, err))) return rc;     // gate-major, stride N
       if ((rc = dalloc(&mask_, N, err))) return rc;
       if ((rc = dalloc(&step_, 1, err))) return rc;
       if ((rc = dalloc(&iters_, cap_, err))) return rc;
@@ -791,7 +791,7 @@ class Engine : public EngineBase {
     const Lev& v0 = lev_[0];
     if (p.scheme == 1 && !up_) {
       if ((rc = dalloc(&up_, N, err))) return rc;
-      if ((rc = dalloc(&wp_, N, err))) return rc;
+      if ((rc = dalloc(&wp_, kMaxGates * N, err))) return rc;
       std::vector<double> minv(me_int_.size());
       if (!spd_inverse_blocks(me_int_.data(), v0.n, B, minv.data())) { err = "element mass block not SPD"; return AGG_ENOTSPD; }
       if ((rc = upload_blocks<double>(minv, v0.n, v0.nsl, &Minv_, err))) return rc;
@@ -825,17 +825,20 @@ class Engine : public EngineBase {
     const Lev& v0 = lev_[0];
     const int64_t g = cdiv(v0.n * B, 256);
     k_gather_units<double, double><<<g, 256, 0, s>>>(u_user, x_, v0.perm, v0.n, B);
-    k_gather_units<double, double><<<g, 256, 0, s>>>(w_user, w_, v0.perm, v0.n, B);
+    const int ng = ionic_gates(sp_.model);
+    const int64_t nu = v0.n * B;                  // caller's DoFs per gate
+    for (int k = 0; k < ng; ++k)
+      k_gather_units<double, double><<<g, 256, 0, s>>>(w_user + k * nu, w_ + k * N0(), v0.perm, v0.n, B);
     AGG_CK(cudaMemcpyAsync(step_, &clock, sizeof(int64_t), cudaMemcpyHostToDevice, s));
     AGG_CK(cudaMemsetAsync(sim_status_, 0, sizeof(int), s));
     if (sp_.scheme == 1 && !hist_valid_) {
       // second-order start of the BDF2 history from the current state
-      IonicParams ip{sp_.model, sp_.k, sp_.a, sp_.eps, sp_.gamma, sp_.mu1, sp_.mu2};
+      IonicParams ip{sp_.model, sp_.k, sp_.a, sp_.eps, sp_.gamma, sp_.mu1, sp_.mu2, sp_.bo};
       const double c = 1.5 * sp_.chi * sp_.cm / sp_.dt;
       const double ia = (clock < sp_.iapp_steps) ? sp_.iapp_value : 0.0;
       k_spmv<double, B, 0, A0Op><<<bgrid(0, v0.nsl), NTB, 0, s>>>(A0f_, x_, nullptr, q_, nullptr, nullptr);
       k_bdf2_start<B><<<bgrid(0, v0.nsl), NTB, 0, s>>>(Minv_, q_, x_, w_, mask_, up_, wp_, ip, sp_.dt, sp_.chi, sp_.cm,
-                                                       c, ia, v0.nsl);
+                                                       c, ia, v0.nsl, N0());
       hist_valid_ = true;
     }
     k_set_opts<<<1, 1, 0, s>>>(st_, sp_.pcg.rtol, sp_.pcg.atol, sp_.pcg.max_it, sp_.pcg.flexible);
@@ -858,7 +861,8 @@ class Engine : public EngineBase {
       done += chunk;
     }
     k_scatter_units<double, double><<<g, 256, 0, s>>>(x_, u_user, v0.perm, v0.n, B);
-    k_scatter_units<double, double><<<g, 256, 0, s>>>(w_, w_user, v0.perm, v0.n, B);
+    for (int k = 0; k < ng; ++k)
+      k_scatter_units<double, double><<<g, 256, 0, s>>>(w_ + k * N0(), w_user + k * nu, v0.perm, v0.n, B);
     AGG_CK(cudaMemcpyAsync(&status, sim_status_, sizeof(int), cudaMemcpyDeviceToHost, s));
     AGG_CK(cudaStreamSynchronize(s));
     AGG_CK(cudaGetLastError());
@@ -927,6 +931,7 @@ class Engine : public EngineBase {
     if (!sim_) { err = "no simulation"; return AGG_EINVAL; }
     if (!Ke_ || !Y_) { err = "the mesh was created without adjoint data (agg_mesh_desc.adjoint_data)"; return AGG_EINVAL; }
     if (sp_.scheme != 0) { err = "the adjoint step is built for the backward-Euler scheme"; return AGG_EUNSUPPORTED; }
+    if (ionic_gates(sp_.model) != 1) { err = "the adjoint step is built for one-gate ionic models"; return AGG_EUNSUPPORTED; }
     int rc;
     const int64_t N = N0();
     if (!ua_) {
@@ -944,7 +949,7 @@ class Engine : public EngineBase {
     k_gather_units<double, double><<<g, 256, 0, s>>>(w_n, wa_, v0.perm, v0.n, B);
     k_gather_units<double, double><<<g, 256, 0, s>>>(u_np1, ub_, v0.perm, v0.n, B);
     k_gather_units<double, double><<<g, 256, 0, s>>>(wbar, wb_, v0.perm, v0.n, B);
-    IonicParams ip{sp_.model, sp_.k, sp_.a, sp_.eps, sp_.gamma, sp_.mu1, sp_.mu2};
+    IonicParams ip{sp_.model, sp_.k, sp_.a, sp_.eps, sp_.gamma, sp_.mu1, sp_.mu2, sp_.bo};
     const double c = sp_.chi * sp_.cm / sp_.dt;
     k_adj_pointwise<B><<<bgrid(k_adj_pointwise<B>, v0.nsl), NTB, 0, s>>>(Me_, x_, ua_, wa_, b_, wb_, ip, sp_.dt, sp_.chi, c, v0.nsl);
     k_grad_logD<B><<<bgrid(k_grad_logD<B>, v0.nsl), NTB, 0, s>>>(A0_, Ke_, Y_, x_, ub_, v0.perm, grad, v0.n);

@@ -295,6 +295,30 @@ class Workload:
 
 FHN = dict(model=0, k=1.0, a=0.13, eps=0.01, gamma=0.5, mu1=0.0, mu2=0.0)
 ALIEV_PANFILOV = dict(model=1, k=8.0, a=0.15, eps=0.002, gamma=0.0, mu1=0.2, mu2=0.3)
+# Bueno-Orovio (Section 2.3.2, Eq. BuenoOrovio) with the values of the paper's
+# appendix table (times in s, u dimensionless), its repeated rows taken once;
+# uo = 0 is the reference potential of the I_so drift term (reading: see
+# oracle/monodomain.py). 3 gating variables.
+BUENO_OROVIO = dict(
+    model=2, k=0.0, a=0.0, eps=0.0, gamma=0.0, mu1=0.0, mu2=0.0,
+    tau1p=6e-2, tau1pp=1.15, tau1plus=1.4506e-3,
+    tau2p=7e-2, tau2pp=2e-2, tau2plus=2.8e-1, tau2inf=7e-2,
+    tau3p=2.7342e-3, tau3pp=3e-3,
+    taufi=1.1e-4, tauo_p=6e-3, tauo_pp=6e-3, tauso_p=4.3e-2, tauso_pp=2e-4, tausi=2.8723e-3,
+    k2=65.0, k3=2.0994, kso=2.0, winf_star=0.94,
+    V1=0.3, V1m=1.5e-2, V2=1.5e-2, V2m=3e-2, V3=0.9087, Vhat=1.58, Vo=6e-3, Vso=0.65, uo=0.0)
+
+def n_gates(ionic: dict) -> int:
+    """Gating variables per DoF of an ionic model: 3 for Bueno-Orovio, else 1."""
+    return 3 if ionic["model"] == 2 else 1
+
+
+def resting_gates(ionic: dict) -> np.ndarray:
+    """Gate values of the resting state u = 0 (one row per gate)."""
+    if ionic["model"] != 2:
+        return np.zeros(1)
+    s_inf = 0.5 * (1.0 + np.tanh(ionic["k3"] * (0.0 - ionic["V3"])))
+    return np.array([1.0, 1.0, s_inf])
 
 
 def square_2d_fhn(n: int = 16, degree: int = 1) -> Workload:
@@ -387,6 +411,27 @@ def ventricle_shell(n_circ=128, n_long=96, n_trans=16, degree: int = 2, n_levels
         n_steps=n_steps, ionic=dict(ALIEV_PANFILOV), stim_elements=stim,
         iapp_value=1.0, iapp_steps=5, rtol=1e-8,
         description="ventricle-like shell, helix fibres, Aliev-Panfilov")
+
+
+def ventricle_shell_bo(n_circ=128, n_long=96, n_trans=16, degree: int = 2, n_levels: int = 5,
+                       n_steps: int = 1000) -> Workload:
+    """The shell of ventricle_shell in metres (inner semi-axes 2.5/2.5/4.5 cm,
+    wall 1 cm) with the Bueno-Orovio model and the conductivities of the
+    paper's Bueno-Orovio table (sigma_l = 1e-4, sigma_t = sigma_n = 0.5e-4
+    m^2/s; sigma_n read as sigma_t), chi_m = C_m = 1, dt = 1e-4 s, stimulus
+    500 /s on the 4 most apical element rows for the first 1 ms (10 steps)."""
+    mesh = shell_mesh(n_circ, n_long, n_trans)
+    mesh = dataclasses.replace(mesh, vertices=mesh.vertices * 0.01)
+    D = conductivity_from_fibres(shell_helix_fibres(mesh), 1.0e-4, 0.5e-4)
+    maps = block_hierarchy(mesh.grid_shape, (2, 2, 2), n_levels)
+    ie = np.indices((n_trans, n_long, n_circ)).reshape(3, -1)
+    stim = ie[1] >= n_long - 4
+    return Workload(
+        name=f"shell_bo_q{degree}_{n_circ}x{n_long}x{n_trans}", mesh=mesh, degree=degree,
+        conductivity=D, maps=maps, penalty_mode=1, penalty_coeff=10.0, dt=1e-4,
+        n_steps=n_steps, ionic=dict(BUENO_OROVIO), stim_elements=stim,
+        iapp_value=500.0, iapp_steps=10, rtol=1e-8,
+        description="ventricle-like shell in metres, helix fibres, Bueno-Orovio")
 
 
 def random_vector(n: int, seed: int) -> np.ndarray:

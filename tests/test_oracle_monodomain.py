@@ -111,3 +111,78 @@ def test_bdf2_second_order_with_ionic_current(prm):
     errs = [abs(final(n) - ref) for n in (32, 64, 128)]
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert rates[-1] > 1.85, (errs, rates)
+
+
+# ---------------------------------------------------------------- Bueno-Orovio (Section 2.3.2)
+
+def _bo_space_clamped(u0, t_end):
+    """Space-clamped model u' = -I_ion(u, w), w' = H(u, w) from rest gates,
+    integrated by an independent stiff solver (scipy LSODA, tight tolerances)."""
+    from scipy.integrate import solve_ivp
+    p = W.BUENO_OROVIO
+
+    def f(t, y):
+        I, H = md.ionic(p, y[:1], y[1:].reshape(3, 1))
+        return np.concatenate([-I, H[:, 0]])
+
+    y0 = np.concatenate([[u0], W.resting_gates(p)])
+    return solve_ivp(f, (0.0, t_end), y0, method="LSODA", rtol=1e-9, atol=1e-11, max_step=1e-4,
+                     dense_output=True)
+
+
+def test_bueno_orovio_rest_is_equilibrium():
+    p = W.BUENO_OROVIO
+    w = W.resting_gates(p)[:, None]
+    I, H = md.ionic(p, np.zeros(1), w)
+    assert I[0] == 0.0 and np.all(H == 0.0)
+    # the drift term as printed, (u - V_o), would leave a current -V_o / tau_o' at rest
+    I2, _ = md.ionic(dict(p, uo=p["Vo"]), np.zeros(1), w)
+    assert I2[0] == pytest.approx(-p["Vo"] / p["tauo_p"])
+
+
+def test_bueno_orovio_gate_rates_above_thresholds():
+    """Above V1 and V2 the a_i vanish: w0, w1 decay at 1/tau1+, 1/tau2+, and
+    w2 relaxes to H^k3_V3(u) at 1/tau3''."""
+    p = W.BUENO_OROVIO
+    u = np.array([1.2, 1.5])
+    w = np.array([[0.3, 0.7], [0.4, 0.9], [0.2, 0.5]])
+    _, H = md.ionic(p, u, w)
+    np.testing.assert_allclose(H[0], -w[0] / p["tau1plus"], rtol=1e-14)
+    np.testing.assert_allclose(H[1], -w[1] / p["tau2plus"], rtol=1e-14)
+    s_inf = 0.5 * (1.0 + np.tanh(p["k3"] * (u - p["V3"])))
+    np.testing.assert_allclose(H[2], (s_inf - w[2]) / p["tau3pp"], rtol=1e-14)
+
+
+def test_bueno_orovio_action_potential():
+    """A supra-threshold start fires a full action potential: fast upstroke to
+    near V^, a plateau of a few hundred ms, repolarisation to rest; a
+    sub-threshold start (below V1) decays without an upstroke."""
+    p = W.BUENO_OROVIO
+    sol = _bo_space_clamped(0.5, 1.0)
+    t = np.linspace(0.0, 1.0, 20001)
+    u = sol.sol(t)[0]
+    assert 1.3 < u.max() <= p["Vhat"]
+    assert t[u.argmax()] < 2e-3
+    above = t[u > 0.1 * u.max()]
+    assert 0.15 < above.max() - above.min() < 0.45
+    assert abs(u[-1]) < 0.05
+    sub = _bo_space_clamped(0.2, 0.2)
+    assert sub.y[0].max() <= 0.2 + 1e-12 and abs(sub.y[0, -1]) < 1e-3
+
+
+def test_bueno_orovio_forward_euler_converges_to_space_clamped_solution():
+    """The oracle's per-step order (gates by forward Euler, then the current
+    with the new gates) converges at first order to the stiff solution."""
+    p = W.BUENO_OROVIO
+    ref = _bo_space_clamped(0.5, 0.05).sol(0.05)[0]
+    errs = []
+    for dt in (2e-5, 1e-5):
+        u = np.array([0.5])
+        w = W.resting_gates(p).reshape(3, 1).copy()
+        for _ in range(int(round(0.05 / dt))):
+            _, H = md.ionic(p, u, w)
+            w = w + dt * H
+            I, _ = md.ionic(p, u, w)
+            u = u - dt * I
+        errs.append(abs(u[0] - ref))
+    assert errs[1] < 1e-2 and 1.6 < errs[0] / errs[1] < 2.4
