@@ -44,6 +44,9 @@ def parse():
                          "and hexahedra of p <= 2, assembled otherwise)")
     ap.add_argument("--workload", default="jsquare2d", choices=list(WORKLOADS))
     ap.add_argument("--n", type=int, default=None, help="elements per direction (box workloads)")
+    ap.add_argument("--agglomeration", default="blocks", choices=["blocks", "rtree"],
+                    help="the workload's structured agglomerates, or the R*-tree's (Section 4.1)")
+    ap.add_argument("--max-entries", type=int, default=8, help="R*-tree node capacity M")
     ap.add_argument("--e2e-steps", type=int, default=None,
                     help="steps of the end-to-end leg (default: --steps; it reruns the timed steps "
                          "from the same state)")
@@ -74,6 +77,10 @@ def workload(args):
     return eval(workload_expr(args))
 
 
+def rtree_m(args):
+    return args.max_entries if args.agglomeration == "rtree" else 0
+
+
 def workload_name(wl):
     cells = "quads" if wl.mesh.dim == 2 else "hexes"
     model = ("FHN", "Aliev-Panfilov", "Bueno-Orovio")[wl.ionic["model"]]
@@ -89,6 +96,11 @@ import numpy as np
 from paper_2602_16312_gb300 import workloads as W
 from oracle import sipg, multigrid as mg, monodomain as md
 wl = {expr}
+if {rtree_M}:
+    import dataclasses
+    from oracle import rtree
+    t = rtree.build(wl.mesh.vertices, wl.mesh.elements, {rtree_M})
+    wl = dataclasses.replace(wl, maps=rtree.agglomeration_maps(t, wl.mesh.n_elements, t.root.level + 1))
 disc = sipg.assemble(wl.mesh.vertices, wl.mesh.elements, wl.conductivity, wl.degree, wl.penalty_mode,
                      wl.penalty_coeff)
 opts = md.StepOptions(dt=wl.dt, ionic=wl.ionic, rtol=wl.rtol, iapp_value=wl.iapp_value, iapp_steps=wl.iapp_steps)
@@ -103,12 +115,12 @@ print(json.dumps(dict(t_step=t_step, iters=res.iterations)))
 """
 
 
-def cpu_oracle_sample(expr):
+def cpu_oracle_sample(expr, rtree_M=0):
     """Runs the oracle single-threaded in a fresh process: one full time step
     (step 0: ionic update, RHS, PCG to 1e-8) of the benchmark workload, timed
     on this host's cores; the oracle's set-up is not timed."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, "-c", ORACLE_SNIPPET.format(root=ROOT, expr=expr)],
+    out = subprocess.run([sys.executable, "-c", ORACLE_SNIPPET.format(root=ROOT, expr=expr, rtree_M=rtree_M)],
                          env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, timeout=1800)
     if out.returncode != 0:
         raise RuntimeError("oracle leg failed: " + out.stderr.decode()[-2000:])
@@ -193,7 +205,7 @@ def run_ours(args, rank, world):
 
     sample = None
     if rank == 0 and not args.no_cpu_baseline:
-        sample = cpu_oracle_sample(workload_expr(args))   # before any GPU work
+        sample = cpu_oracle_sample(workload_expr(args), rtree_m(args))   # before any GPU work
 
     from paper_2602_16312_gb300 import aggmg, build
     build.build()
@@ -205,6 +217,9 @@ def run_ours(args, rank, world):
         args.fine = "mf" if (args.form != "f64" and mf_ok) else "bsr"
     t0 = time.time()
     mesh = aggmg.Mesh.from_workload(wl)
+    if args.agglomeration == "rtree":                # nested agglomerates from the mesh's R*-tree
+        import dataclasses
+        wl = dataclasses.replace(wl, maps=aggmg.rtree_maps(mesh, args.max_entries))
     hier = aggmg.Hierarchy(mesh, 1.0 / wl.dt, wl.maps, precision=args.form, fine=args.fine)
     setup_s = time.time() - t0
     if args.profile_kernel is not None:
@@ -303,11 +318,12 @@ def run_ours(args, rank, world):
     st = hier.stats()
     L = hier.n_levels
     vcyc = (L - 1) * 9 + 2
-    per_iter = 6 + vcyc + (1 if args.form != "f64" else 0)
+    body = 5 + vcyc                                            # SpMV+dot, update, V-cycle, dot, p, loop control
+    init = 7 + vcyc + (1 if args.form != "f64" else 0)        # begin, residual, norm, [cast], V-cycle, dot, p, loop
     n_iter = sum(its)
-    # per step: ionic/RHS, set-up (begin, residual, norm, V-cycle, dot, p, loop control),
-    # one body per iteration (the body that detects convergence included), step end
-    launches = args.steps * (1 + per_iter + 1) + n_iter * per_iter + 5
+    # per step: ionic/RHS, the solve's set-up, one body per iteration (the body
+    # that detects convergence included), step end
+    launches = args.steps * (1 + init + 1) + n_iter * body + 5
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
@@ -317,6 +333,8 @@ def run_ours(args, rank, world):
         "data": "synthetic",
         "mdof_per_s": N * total_steps / t / 1e6,
         "config": {"workload": workload_name(wl), "form": args.form, "fine_operator": args.fine,
+                   "agglomeration": args.agglomeration if args.agglomeration == "blocks"
+                   else f"R*-tree, M = {args.max_entries}",
                    "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2 (fine float64 matrix {k0bytes / 1e9:.2f} GB, 129 MB L2)",
                    "levels": st["units"], "op_complexity": st["op_complexity"], "setup_s": setup_s,
@@ -343,7 +361,7 @@ def run_reference(args, rank):
     """The oracle as it stands, on the host cores, as the reference arm."""
     if rank != 0:
         return
-    sample = cpu_oracle_sample(workload_expr(args))
+    sample = cpu_oracle_sample(workload_expr(args), rtree_m(args))
     wl = workload(args)
     base = cpu_baseline_entry(sample, wl.name)
     line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": 1,

@@ -202,6 +202,28 @@ agg_status agg_vcycle_apply(agg_hier_t hier, const double* r_dev, double* z_dev,
 agg_status agg_operator_apply_static(agg_hier_t hier, int level, const double* x_dev, double* y_dev,
                                      void* stream);
 
+/* ------------------------------------------------------------------ agglomeration
+ * R*-tree agglomeration (Section 4.1, Algorithms 1 and 2), on the host. The
+ * elements' axis-aligned bounding boxes (of their corner vertices) are
+ * inserted in element order into an R*-tree holding at most max_entries
+ * (>= 4) entries per node, with the insertion algorithm of Beckmann et al.
+ * (choose-subtree by least overlap enlargement just above the leaves and
+ * least area enlargement higher up; one forced reinsert of the 30% farthest
+ * entries per tree level and inserted element; split on the axis of least
+ * margin sum at the distribution of least overlap; minimum fill 40%). The
+ * nodes of height h agglomerate the elements below them; heights 0, 1, ...
+ * give nested levels: maps[0][e] = leaf node of element e, and for k >= 1
+ * maps[k][i] = parent of node i of height k-1, nodes numbered depth-first
+ * from the root. maps: n_maps caller-owned host arrays of at least
+ * n_elements int32 each (maps[k] is filled up to n_units[k-1] entries,
+ * maps[0] up to n_elements); n_units[k] receives the units of level k+1;
+ * tree_levels (may be NULL) the number of node levels. The result can be
+ * passed as agg_mg_opts.agg_maps with n_levels = n_maps + 1. Errors:
+ * AGG_EINVAL for max_entries < 4, n_maps above the tree's levels or NULL
+ * arrays (with n_maps = 0 the call only reports tree_levels). */
+agg_status agg_rtree_agglomerate(agg_mesh_t mesh, int max_entries, int n_maps, int32_t* const* maps,
+                                 int64_t* n_units, int* tree_levels);
+
 /* ------------------------------------------------------------------ ionic models */
 typedef enum { AGG_FHN = 0, AGG_ALIEV_PANFILOV = 1, AGG_BUENO_OROVIO = 2 } agg_ionic_model;
 

@@ -91,6 +91,8 @@ _SIGS = {
     "agg_vcycle_apply": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "agg_operator_apply_static": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p],
     "agg_ionic_update": [C.POINTER(IonicParams), C.c_double, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
+    "agg_rtree_agglomerate": [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.POINTER(C.c_int32)),
+                              C.POINTER(C.c_int64), C.POINTER(C.c_int)],
     "agg_monodomain_create": [C.c_void_p, C.POINTER(SimOpts), C.POINTER(C.c_void_p)],
     "agg_monodomain_step": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.c_void_p],
     "agg_monodomain_set_clock": [C.c_void_p, C.c_int64],
@@ -365,6 +367,20 @@ class Hierarchy:
             self.close()
         except Exception:
             pass
+
+
+def rtree_maps(mesh, max_entries=8, n_maps=None):
+    """agg_rtree_agglomerate: the nested agglomeration maps of the mesh's
+    R*-tree (all node levels when n_maps is None), as int32 arrays."""
+    levels = C.c_int()
+    _check(lib().agg_rtree_agglomerate(mesh.handle, max_entries, 0, None, None, C.byref(levels)))
+    n_maps = levels.value if n_maps is None else n_maps
+    bufs = [np.full(mesh.n_elements, -1, dtype=np.int32) for _ in range(n_maps)]
+    ptrs = (C.POINTER(C.c_int32) * max(n_maps, 1))(*[b.ctypes.data_as(C.POINTER(C.c_int32)) for b in bufs])
+    units = (C.c_int64 * max(n_maps, 1))()
+    _check(lib().agg_rtree_agglomerate(mesh.handle, max_entries, n_maps, ptrs, units, C.byref(levels)))
+    sizes = [mesh.n_elements] + [units[k] for k in range(n_maps)]
+    return [bufs[k][:sizes[k]].copy() for k in range(n_maps)]
 
 
 def n_gates(d: dict) -> int:

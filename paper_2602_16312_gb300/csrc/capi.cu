@@ -149,6 +149,15 @@ agg_status agg_dg_mesh_locate(agg_mesh_t mh, int64_t n, const double* pts, int64
   return AGG_OK;
 }
 
+agg_status agg_rtree_agglomerate(agg_mesh_t mh, int max_entries, int n_maps, int32_t* const* maps,
+                                 int64_t* n_units, int* tree_levels) {
+  if (!mh || n_maps < 0) return fail(AGG_EINVAL, "bad argument");
+  std::string err;
+  int rc = rtree_agglomerate(mh->m, max_entries, n_maps, maps, n_units, tree_levels, err);
+  if (rc) return fail((agg_status)rc, err);
+  return AGG_OK;
+}
+
 agg_status agg_dg_mesh_nnzb(agg_mesh_t m, int64_t* nnzb) {
   if (!m || !nnzb) return fail(AGG_EINVAL, "NULL argument");
   *nnzb = m->m.A.nnzb();

@@ -77,23 +77,36 @@ static __global__ void __launch_bounds__(RED_NT) k_r0(const double* __restrict__
   }
 }
 
-// x += alpha p; r -= alpha q; ||r||; convergence test
+// x += alpha p; r -= alpha q; ||r||; convergence test. Fused with the
+// V-cycle's input cast (r32 = (float) r, when r32 is given) and, for the
+// flexible variant, the (r_new, z_old) product of the Polak-Ribiere beta
+// (z_old: the previous preconditioned residual). Both sums use the fixed
+// grid and block order of the other reductions (second sum in
+// partials[gridDim.x ..]).
 static __global__ void __launch_bounds__(RED_NT) k_cg_update(double* __restrict__ x, double* __restrict__ r,
                                                       const double* __restrict__ p, const double* __restrict__ q,
+                                                      float* __restrict__ r32, const double* __restrict__ zold,
                                                       int64_t n, double* partials, CGState* st) {
   if (st->done) return;
   const double alpha = st->alpha;
-  double s = 0.0;
+  const bool flex = st->flexible != 0;
+  double s = 0.0, sz = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * RED_NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_NT) {
     x[i] += alpha * p[i];
     double ri = r[i] - alpha * q[i];
     r[i] = ri;
     s += ri * ri;
+    if (flex) sz += ri * zold[i];
+    if (r32) r32[i] = (float)ri;
   }
+  const double bz = block_sum<RED_NT>(sz);
+  if (threadIdx.x == 0) partials[gridDim.x + blockIdx.x] = bz;
   if (partial_and_last<RED_NT>(s, partials, &st->ticket[TK_R])) {
     double rr = sum_partials<RED_NT>(partials, gridDim.x);
+    double rz = sum_partials<RED_NT>(partials + gridDim.x, gridDim.x);
     if (threadIdx.x == 0) {
       st->ticket[TK_R] = 0;
+      if (flex) st->rz_old = rz;
       st->rr = rr;
       st->iter += 1;
       double rn = sqrt(rr);
@@ -113,7 +126,7 @@ static __global__ void __launch_bounds__(RED_NT) k_cg_update(double* __restrict_
 // z64 <- zin (V-cycle output, any precision); rz = (r, z_new).
 // INIT: rho = rz.  Otherwise beta = rz / rho (Fletcher-Reeves form) or, for
 // the flexible variant, beta = (rz - (r, z_old)) / rho (Polak-Ribiere, with
-// (r, z_old) from k_flex_beta), then rho = rz.
+// (r, z_old) from k_cg_update), then rho = rz.
 template <typename TZ, bool INIT>
 static __global__ void __launch_bounds__(RED_NT) k_zdot(const TZ* __restrict__ zin, double* __restrict__ z64,
                                                  const double* __restrict__ r, int64_t n, double* partials,
@@ -132,23 +145,6 @@ static __global__ void __launch_bounds__(RED_NT) k_zdot(const TZ* __restrict__ z
       if (INIT) st->beta = 0.0;
       else st->beta = (st->flexible ? rz - st->rz_old : rz) / st->rho;
       st->rho = rz;
-    }
-  }
-}
-
-// Flexible (Polak-Ribiere) beta needs (r, z_old) of all blocks: done by a
-// separate pass so the partials of both sums are complete.
-static __global__ void __launch_bounds__(RED_NT) k_flex_beta(const double* __restrict__ r, const double* __restrict__ zold,
-                                                      int64_t n, double* partials, CGState* st) {
-  if (st->done || !st->flexible) return;
-  double s = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * RED_NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_NT)
-    s += r[i] * zold[i];
-  if (partial_and_last<RED_NT>(s, partials, &st->ticket[TK_PQ])) {
-    double so = sum_partials<RED_NT>(partials, gridDim.x);
-    if (threadIdx.x == 0) {
-      st->ticket[TK_PQ] = 0;
-      st->rz_old = so;
     }
   }
 }

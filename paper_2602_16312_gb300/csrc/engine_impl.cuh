@@ -354,16 +354,17 @@ class Engine : public EngineBase {
   bool use_mf0() const { return kMf && mf_; }
   int64_t g0() const { return cdiv(lev_[0].nsl * SL, NTB); }
 
+  // z = V(r), beta, p. In the iteration body the float32 cast of r and the
+  // flexible-beta product (r, z_old) come fused in k_cg_update.
   void launch_precond(cudaStream_t s, bool init) {
     const int64_t N = N0();
-    if (!std::is_same<T, double>::value)
+    if (init && !std::is_same<T, double>::value)
       k_cast<float, double><<<RED_BLOCKS, RED_NT, 0, s>>>(r_, r32_, N, st_);
     T* out = vc(0, s);
     if (init) {
       k_zdot<T, true><<<RED_BLOCKS, RED_NT, 0, s>>>(out, z_, r_, N, partials_, st_);
       k_pupd<true><<<RED_BLOCKS, RED_NT, 0, s>>>(z_, p_, N, st_);
     } else {
-      k_flex_beta<<<RED_BLOCKS, RED_NT, 0, s>>>(r_, z_, N, partials_, st_);
       k_zdot<T, false><<<RED_BLOCKS, RED_NT, 0, s>>>(out, z_, r_, N, partials_, st_);
       k_pupd<false><<<RED_BLOCKS, RED_NT, 0, s>>>(z_, p_, N, st_);
     }
@@ -379,7 +380,8 @@ class Engine : public EngineBase {
 
   void launch_body(cudaStream_t s) {
     k_spmv<double, B, 2, A0Op><<<bgrid(0, lev_[0].nsl), NTB, 0, s>>>(A0f_, p_, nullptr, q_, partials_, st_);
-    k_cg_update<<<RED_BLOCKS, RED_NT, 0, s>>>(x_, r_, p_, q_, N0(), partials_, st_);
+    k_cg_update<<<RED_BLOCKS, RED_NT, 0, s>>>(x_, r_, p_, q_, std::is_same<T, double>::value ? nullptr : r32_, z_,
+                                              N0(), partials_, st_);
     launch_precond(s, false);
     k_loop_ctl<<<1, 1, 0, s>>>(st_);
   }

@@ -142,6 +142,13 @@ struct FaceBlocks {
 // Fails (AGG_EINVAL) if an entry outside these parts is nonzero.
 int face_blocks_build(const Mesh& m, const HostLevel& l0, FaceBlocks& out, std::string& err);
 
+// R*-tree agglomeration of the mesh's elements (Section 4.1, Algorithms 1
+// and 2): maps[k] of the k-th multigrid level (k = 0: elements -> leaf
+// nodes; k >= 1: nodes of height k-1 -> their parents), n_units[k] = units
+// of level k+1, *height = node levels of the tree.
+int rtree_agglomerate(const Mesh& m, int max_entries, int n_maps, int32_t* const* maps, int64_t* n_units,
+                      int* height, std::string& err);
+
 // inverses of n SPD B x B row-major blocks (Cholesky); false if one is not SPD
 bool spd_inverse_blocks(const double* blocks, int64_t n, int B, double* out);
 
