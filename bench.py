@@ -67,6 +67,16 @@ WORKLOADS = {
 }
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# dominant kernel, from one ncu capture of the same configuration and kernel
+# code, with the summary that records the command: (workload, form, level-0
+# operator, agglomeration, kernel id) -> (bytes, summary). Other
+# configurations report null.
+NCU_TRAFFIC = {
+    ("jsquare2d_q2_512x512", "f32", "mf", "blocks", 1): (247.04e6, "profiles/k_cheb_mf_jsquare2d_q2_512.md"),
+}
+
+
 def workload_expr(args):
     expr, n0 = WORKLOADS[args.workload]
     return expr.format(n=args.n if args.n is not None else n0)
@@ -306,6 +316,9 @@ def run_ours(args, rank, world):
         roof = {"bound": "hbm", "achieved": kbytes / t_k / 1e9, "peak": hbm, "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
+    cap = NCU_TRAFFIC.get((wl.name, args.form, args.fine, args.agglomeration, kid))
+    if cap is not None:
+        roof["traffic"], roof["traffic_source"] = cap
     roof["kernel"] = KERNEL_NAMES_MF[kid] if args.fine == "mf" else KERNEL_NAMES[kid]
     roof["us_per_launch"] = t_k * 1e6
     roof["algorithmic_bytes"] = kbytes
