@@ -19,10 +19,21 @@ EngineBase* make_engine_b4(int);
 EngineBase* make_engine_b8(int);
 EngineBase* make_engine_b9(int);
 EngineBase* make_engine_b16(int);
-EngineBase* make_engine_b27(int);
+EngineBase* make_engine_b27_f64();
+EngineBase* make_engine_b27_f32();
+EngineBase* make_engine_b27_bf16();
 EngineBase* make_engine_b64_f64();
 EngineBase* make_engine_b64_f32();
 EngineBase* make_engine_b64_bf16();
+
+static EngineBase* make_engine_b27(int precision) {
+  switch (precision) {
+    case AGG_F64: return make_engine_b27_f64();
+    case AGG_F32: return make_engine_b27_f32();
+    case AGG_F32_BF16SMOOTH: return make_engine_b27_bf16();
+    default: return nullptr;
+  }
+}
 
 static EngineBase* make_engine_b64(int precision) {
   switch (precision) {
