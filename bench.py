@@ -15,6 +15,7 @@ Prints one JSON line (rank 0).
 import argparse
 import json
 import os
+import resource
 import statistics
 import subprocess
 import sys
@@ -47,6 +48,8 @@ def parse():
     ap.add_argument("--agglomeration", default="blocks", choices=["blocks", "rtree"],
                     help="the workload's structured agglomerates, or the R*-tree's (Section 4.1)")
     ap.add_argument("--max-entries", type=int, default=8, help="R*-tree node capacity M")
+    ap.add_argument("--adjoint-steps", type=int, default=0,
+                    help="also time this many reverse (adjoint) steps after as many forward steps")
     ap.add_argument("--e2e-steps", type=int, default=None,
                     help="steps of the end-to-end leg (default: --steps; it reruns the timed steps "
                          "from the same state)")
@@ -226,7 +229,7 @@ def run_ours(args, rank, world):
         mf_ok = wl.degree <= (3 if wl.mesh.dim == 2 else 2)
         args.fine = "mf" if (args.form != "f64" and mf_ok) else "bsr"
     t0 = time.time()
-    mesh = aggmg.Mesh.from_workload(wl)
+    mesh = aggmg.Mesh.from_workload(wl, adjoint_data=args.adjoint_steps > 0)
     if args.agglomeration == "rtree":                # nested agglomerates from the mesh's R*-tree
         import dataclasses
         wl = dataclasses.replace(wl, maps=aggmg.rtree_maps(mesh, args.max_entries))
@@ -291,6 +294,31 @@ def run_ours(args, rank, world):
     e2e_same = None
     if args.e2e_steps == args.steps:
         e2e_same = bool(torch.equal(uh.to(dev), u_end))     # bitwise: deterministic reductions
+    # ---- reverse (adjoint) steps: K forward steps keep their states, then K
+    # reverse steps from a seeded dL/du at the end accumulate the per-element
+    # log-conductivity gradient (the adjoint form's per-step work)
+    adjoint = None
+    if args.adjoint_steps > 0:
+        K = args.adjoint_steps
+        us, ws = [u.clone()], [w.clone()]
+        for _ in range(K):
+            sim.step(u, w, 1)
+            us.append(u.clone())
+            ws.append(w.clone())
+        gen = torch.Generator(device=dev).manual_seed(4)
+        ubar = torch.randn(N, dtype=torch.float64, device=dev, generator=gen)
+        wbar = torch.zeros_like(w)
+        grad = torch.zeros(mesh.n_elements, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for k in reversed(range(K)):
+            sim.adjoint_step(us[k], ws[k], us[k + 1], ubar, wbar, grad)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_adj = ev0.elapsed_time(ev1) / 1e3
+        adjoint = {"value": K / t_adj, "unit": "reverse time-steps/s", "steps": K,
+                   "ms_per_step": 1e3 * t_adj / K, "grad_finite": bool(torch.isfinite(grad).all())}
+        del us, ws
     # ---- dominant kernel, timed live with events on the launching stream
     kid = 1
     reps = 50
@@ -361,6 +389,8 @@ def run_ours(args, rank, world):
         "roofline": roof, "fine_fp64_spmv": other,
         "gpu_launches": launches,
         "clocks": clk.summary(),
+        "host_peak_rss_gb": resource.getrusage(resource.RUSAGE_SELF).ru_maxrss / 2**20,
+        **({"adjoint": adjoint} if adjoint is not None else {}),
     }
     if sample is not None:
         line["cpu_baseline"] = cpu_baseline_entry(sample, wl.name)

@@ -188,7 +188,7 @@ agg_status agg_dg_mesh_copy(agg_mesh_t mh, int what, void* dst) {
     case 6:
       if (!m.adjoint_data) return fail(AGG_EINVAL, "mesh has no adjoint data");
       if (what == 5) std::memcpy(dst, m.Ke.data(), sizeof(double) * m.Ke.size());
-      else std::memcpy(dst, m.Y.data(), sizeof(double) * m.Y.size());
+      else adjoint_face_parts_full(m, static_cast<double*>(dst));
       break;
     default: return fail(AGG_EINVAL, "what");
   }

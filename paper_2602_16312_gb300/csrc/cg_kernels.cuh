@@ -5,6 +5,7 @@
 // per block and the last block to finish sums them in block order.
 #pragma once
 #include "../../include/aggmg.h"
+#include "face_op.cuh"
 #include "kernels.cuh"
 
 namespace aggmg {
@@ -477,47 +478,79 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
   }
 }
 
+// Layout of the adjoint face parts on the device: per slice and local face,
+// five row-major parts (the structure of Mesh::Yc), each padded to whole
+// double2 chunks, in the sliced chunk order [chunk][lane][2].
+template <int B> struct AdjFaceLayout {
+  static constexpr int NF = FaceIdx<FaceShape<B>::D, FaceShape<B>::N>::NF;
+  static constexpr int P1 = (NF * B + 1) / 2 * 2, P2 = ((B - NF) * NF + 1) / 2 * 2, P3 = (B * NF + 1) / 2 * 2;
+  static constexpr int P4 = P1, P5 = (NF * NF + 1) / 2 * 2;
+  static constexpr int YS = P1 + P2 + P3 + P4 + P5;      // doubles per lane and face
+};
+
+// sum_{r, c} y(r) M[r][c] x(c) over one R x C part starting at chunk ch0
+template <int R, int C, typename YF, typename XF>
+__device__ __forceinline__ double part_bilinear(const double2* yb, int ch0, YF y, XF x) {
+  double s = 0.0;
+#pragma unroll 1
+  for (int ch = 0; ch < (R * C + 1) / 2; ++ch) {
+    const double2 v = __ldg(yb + (size_t)(ch0 + ch) * SL);
+    const int k = 2 * ch;
+    s += v.x * y(k / C) * x(k % C);
+    if (k + 1 < R * C) s += v.y * y((k + 1) / C) * x((k + 1) % C);
+  }
+  return s;
+}
+
 // Per-element log-conductivity gradient, accumulated in the caller's order:
 //   grad[e] -= lam_e^T Ke u_e + sum_faces [lam_e; lam_n]^T Y_e,F [u_e; u_n]
-// with Ke the volume form and Y_e,F the face terms built with D_e (four
-// sliced blocks per stiffness slot, in the slot order of the fine operator).
+// with Ke the volume form and Y_e,F the face terms built with D_e, of which
+// only the trace-structured parts are stored (AdjFaceLayout): ee on e's face
+// rows and face columns, en on n's face columns, ne on n's face rows, nn.
 template <int B>
 static __global__ void __launch_bounds__(UnitThreads<B>::value)
-    k_grad_logD(SellView<double> A, const double* __restrict__ Ke, const double* __restrict__ Y,
+    k_grad_logD(FaceView<double, B> F, const double* __restrict__ Ke, const double* __restrict__ Yc,
                 const double* __restrict__ lam, const double* __restrict__ u, const int64_t* __restrict__ perm,
                 double* __restrict__ grad, int64_t n) {
   constexpr int NTB = UnitThreads<B>::value;
   constexpr int KP = Pad<double, B>::KP;
+  using FI = FaceIdx<FaceShape<B>::D, FaceShape<B>::N>;
+  using YL = AdjFaceLayout<B>;
+  constexpr int NF = YL::NF, NFACE = 2 * FaceShape<B>::D;
   const int lane = threadIdx.x & 31;
-  {
   const int64_t slice = first_slice<NTB>();
-  if (slice >= A.nslices) return;
+  if (slice >= F.nslices) return;
   const int64_t unit = slice * SL + lane;
   const size_t o = (size_t)unit * B;
-  // sum_r l[r] (M1 x1 + M2 x2)[r] for two sliced blocks (M2 may be null)
-  auto bilin = [&](const double* l, const double* M1, const double* x1, const double* M2, const double* x2) {
-    double t[B];
+  double t[B];
 #pragma unroll
-    for (int r = 0; r < B; ++r) t[r] = 0.0;
-    block_mv<double, double, B>(M1, lane, x1, t);
-    if (M2) block_mv<double, double, B>(M2, lane, x2, t);
-    double s = 0.0;
+  for (int r = 0; r < B; ++r) t[r] = 0.0;
+  block_mv<double, double, B>(Ke + (size_t)slice * SL * KP, lane, u + o, t);
+  double g = 0.0;
 #pragma unroll
-    for (int r = 0; r < B; ++r) s += l[r] * t[r];
-    return s;
-  };
-  double g = bilin(lam + o, Ke + (size_t)slice * SL * KP, u + o, nullptr, nullptr);
-  const int s0 = A.slice_ptr[slice], s1 = A.slice_ptr[slice + 1];
-  for (int j = s0; j < s1; ++j) {
-    const int col = A.cols[(size_t)j * SL + lane];
-    if (col == unit) continue;                 // diagonal or padding slot
-    const double* Yj = Y + (size_t)j * 4 * SL * KP;
-    const double* un = u + (size_t)col * B;
-    g += bilin(lam + o, Yj, u + o, Yj + (size_t)SL * KP, un);
-    g += bilin(lam + (size_t)col * B, Yj + (size_t)2 * SL * KP, u + o, Yj + (size_t)3 * SL * KP, un);
+  for (int r = 0; r < B; ++r) g += lam[o + r] * t[r];
+  const double* lu = lam + o;
+  const double* uu = u + o;
+#pragma unroll 1
+  for (int f = 0; f < NFACE; ++f) {
+    const size_t fi = ((size_t)slice * NFACE + f) * SL + lane;
+    const int nb = F.nbr[fi];
+    if (nb < 0) continue;
+    const int fn = F.code[fi];
+    const double* ln = lam + (size_t)nb * B;
+    const double* un = u + (size_t)nb * B;
+    const double2* yb = reinterpret_cast<const double2*>(Yc) + ((size_t)(slice * NFACE + f) * (YL::YS / 2)) * SL + lane;
+    g += part_bilinear<NF, B>(yb, 0, [&](int r) { return lu[FI::face(f, r)]; }, [&](int c) { return uu[c]; });
+    g += part_bilinear<B - NF, NF>(yb, YL::P1 / 2, [&](int r) { return lu[FI::off(f, r)]; },
+                                   [&](int c) { return uu[FI::face(f, c)]; });
+    g += part_bilinear<B, NF>(yb, (YL::P1 + YL::P2) / 2, [&](int r) { return lu[r]; },
+                              [&](int c) { return un[FI::face(fn, c)]; });
+    g += part_bilinear<NF, B>(yb, (YL::P1 + YL::P2 + YL::P3) / 2, [&](int r) { return ln[FI::face(fn, r)]; },
+                              [&](int c) { return uu[c]; });
+    g += part_bilinear<NF, NF>(yb, (YL::P1 + YL::P2 + YL::P3 + YL::P4) / 2,
+                               [&](int r) { return ln[FI::face(fn, r)]; }, [&](int c) { return un[FI::face(fn, c)]; });
   }
   if (unit < n) grad[perm[unit]] -= g;
-  }
 }
 
 // end of a time step: record the iteration count, advance the clock

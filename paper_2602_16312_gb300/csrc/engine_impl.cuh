@@ -585,29 +585,40 @@ class Engine : public EngineBase {
       for (int64_t r = 0; r < m.ne; ++r)
         std::memcpy(&ke[(size_t)r * B * B], &m.Ke[(size_t)l0.perm[r] * B * B], sizeof(double) * B * B);
       if ((rc = upload_blocks<double>(ke, m.ne, lev_[0].nsl, &Ke_, err))) return rc;
-      constexpr int KP = Pad<double, B>::KP;
+      // face parts per (slice, local face), the five parts padded to whole
+      // double2 chunks, in the chunk layout (see k_grad_logD); copied in
+      // pieces of 1024 slices so the host needs no full-size staging copy
+      using YL = AdjFaceLayout<B>;
+      const int nf = 2 * FaceShape<B>::D, NF = YL::NF;
       const int64_t nsl = lev_[0].nsl;
-      std::vector<int64_t> sp(nsl + 1, 0);
-      for (int64_t sl = 0; sl < nsl; ++sl) {
-        int64_t mx = 1;
-        for (int64_t u = sl * SL; u < std::min<int64_t>(m.ne, (sl + 1) * SL); ++u)
-          mx = std::max<int64_t>(mx, l0.A.rowptr[u + 1] - l0.A.rowptr[u]);
-        sp[sl + 1] = sp[sl] + mx;
-      }
-      std::vector<double> hy((size_t)sp[nsl] * 4 * SL * KP, 0.0);
-      for (int64_t r = 0; r < m.ne; ++r) {
-        const int64_t e = l0.perm[r];
-        std::vector<std::pair<int64_t, int64_t>> cols;
-        for (int64_t k = m.A.rowptr[e]; k < m.A.rowptr[e + 1]; ++k) cols.push_back({l0.inv[m.A.col[k]], k});
-        std::sort(cols.begin(), cols.end());
-        for (size_t j = 0; j < cols.size(); ++j) {
-          const int64_t slot = sp[r / SL] + (int64_t)j;
-          for (int b = 0; b < 4; ++b)
-            pack<double>(&m.Y[((size_t)cols[j].second * 4 + b) * B * B], &hy[((size_t)slot * 4 + b) * SL * KP],
-                         (int)(r % SL));
+      const size_t per_slice = (size_t)nf * YL::YS * SL;
+      if ((rc = dalloc(&Y_, (size_t)nsl * per_slice, err))) return rc;
+      const int sizes[5] = {NF * B, (B - NF) * NF, B * NF, NF * B, NF * NF};
+      const int offs[5] = {0, YL::P1, YL::P1 + YL::P2, YL::P1 + YL::P2 + YL::P3, YL::P1 + YL::P2 + YL::P3 + YL::P4};
+      const int64_t piece = 1024;
+      std::vector<double> hy;
+      for (int64_t s0 = 0; s0 < nsl; s0 += piece) {
+        const int64_t s1 = std::min(nsl, s0 + piece);
+        hy.assign((size_t)(s1 - s0) * per_slice, 0.0);
+        for (int64_t r = s0 * SL; r < std::min<int64_t>(m.ne, s1 * SL); ++r) {
+          const int64_t e = l0.perm[r], sl = r / SL - s0;
+          const int lane = (int)(r % SL);
+          for (int f = 0; f < nf; ++f) {
+            const double* src = &m.Yc[((size_t)e * nf + f) * 4 * NF * B];
+            double* dst = &hy[((size_t)sl * nf + f) * YL::YS * SL];
+            int so = 0;
+            for (int pt = 0; pt < 5; ++pt) {
+              for (int k = 0; k < sizes[pt]; ++k) {
+                const int kk = offs[pt] + k;
+                dst[((size_t)(kk / 2) * SL + lane) * 2 + (kk % 2)] = src[so + k];
+              }
+              so += sizes[pt];
+            }
+          }
         }
+        AGG_CK(cudaMemcpy(Y_ + (size_t)s0 * per_slice, hy.data(), sizeof(double) * hy.size(),
+                          cudaMemcpyHostToDevice));
       }
-      if ((rc = upload(&Y_, hy.data(), hy.size(), err))) return rc;
     }
     // matrix-free fine operator for the float32 V-cycle
     if (fine_operator == 1) {
@@ -954,7 +965,7 @@ class Engine : public EngineBase {
     IonicParams ip{sp_.model, sp_.k, sp_.a, sp_.eps, sp_.gamma, sp_.mu1, sp_.mu2, sp_.bo};
     const double c = sp_.chi * sp_.cm / sp_.dt;
     k_adj_pointwise<B><<<bgrid(k_adj_pointwise<B>, v0.nsl), NTB, 0, s>>>(Me_, x_, ua_, wa_, b_, wb_, ip, sp_.dt, sp_.chi, c, v0.nsl);
-    k_grad_logD<B><<<bgrid(k_grad_logD<B>, v0.nsl), NTB, 0, s>>>(A0_, Ke_, Y_, x_, ub_, v0.perm, grad, v0.n);
+    k_grad_logD<B><<<bgrid(0, v0.nsl), NTB, 0, s>>>(A0f_.V, Ke_, Y_, x_, ub_, v0.perm, grad, v0.n);
     k_scatter_units<double, double><<<g, 256, 0, s>>>(b_, ubar, v0.perm, v0.n, B);
     k_scatter_units<double, double><<<g, 256, 0, s>>>(wb_, wbar, v0.perm, v0.n, B);
     AGG_CK(cudaMemcpyAsync(st_host_, st_, sizeof(CGState), cudaMemcpyDeviceToHost, s));

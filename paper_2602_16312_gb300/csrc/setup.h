@@ -42,9 +42,14 @@ struct Mesh {
   std::vector<double> Me;        // [ne][B][B] element mass blocks
   std::vector<double> vol;       // [ne]
   int64_t n_faces = 0;           // interior faces
-  // adjoint data (when adjoint_data): per stiffness block k of row e with
-  // column n != e, the four blocks (ee, en, ne, nn) of the face terms built
-  // with D_e; with Ke the volume form, sum_e of these parts is A.
+  // adjoint data (when adjoint_data): per element e and local face f with
+  // neighbour n (local face fn), the four blocks (ee, en, ne, nn) of the face
+  // terms built with D_e (with Ke the volume form, sum_e of these parts is A),
+  // keeping only what a GLL nodal basis can make nonzero, NF = N^(d-1):
+  //   Yc[(e*2d + f)*4*NF*B ..]: ee rows on face f (NF x B), ee other rows x
+  //   face-f columns ((B-NF) x NF), en all rows x n's face-fn columns (B x NF),
+  //   ne n's face-fn rows x all columns (NF x B), nn (NF x NF); row-major, face
+  //   and off-face DoFs ordered as in FaceBlocks.
   bool adjoint_data = false;
   // face neighbours: face_nbr[e*2d + f] = n*2d + fn for an interior face, -1
   // on the boundary; face_rev: 1 when the neighbour runs the shared face in
@@ -55,8 +60,12 @@ struct Mesh {
   // the coupling through face f alone (-1 on the boundary)
   std::vector<int32_t> face_slot;
   std::vector<double> Ke;        // [ne][B][B]
-  std::vector<double> Y;         // [nnzb][4][B][B]
+  std::vector<double> Yc;        // [ne][2d][4 NF B]
 };
+
+// The adjoint face parts expanded to full blocks, [nnzb][4][B][B] in the
+// stiffness slot order (zero in the diagonal slots and off the trace parts).
+void adjoint_face_parts_full(const Mesh& m, double* out);
 
 // Element and interpolation weights of each point (Newton on the element map).
 int mesh_locate(const Mesh& m, int64_t n, const double* pts, int64_t* elem, double* weights,

@@ -201,6 +201,23 @@ int face_corners(int dim, int f, int* out) {
   return nvf;
 }
 
+int axis_stride(int N, int a) { return a == 0 ? 1 : (a == 1 ? N : N * N); }
+// r-th DoF on local face f (r = j1 + N j2 over the tangential axes in increasing order)
+int face_dof(int dim, int N, int f, int r) {
+  const int k = f / 2, s = f % 2;
+  int t[2] = {0, 0}, no = 0;
+  for (int a = 0; a < dim; ++a)
+    if (a != k) t[no++] = a;
+  int idx = s * (N - 1) * axis_stride(N, k) + (r % N) * axis_stride(N, t[0]);
+  if (dim == 3) idx += (r / N) * axis_stride(N, t[1]);
+  return idx;
+}
+// r-th DoF off local face f (r = j1 + N j2 + NF i', i' the normal index with
+// the face layer left out)
+int off_dof(int dim, int N, int f, int r) {
+  const int k = f / 2, s = f % 2, NF = dim == 2 ? N : N * N;
+  return (r / NF + 1 - s) * axis_stride(N, k) + face_dof(dim, N, 2 * k, r % NF);
+}
 }  // namespace
 
 // ---------------------------------------------------------------- assembly
@@ -361,7 +378,8 @@ int mesh_build(Mesh& m, std::string& err) {
   m.A.col.assign(nnzb, 0);
   m.A.val.assign((size_t)nnzb * B * B, 0.0);
   m.face_slot.assign((size_t)ne * nf, -1);
-  if (adj) m.Y.assign((size_t)nnzb * 4 * B * B, 0.0);
+  const int NFd = (dim == 2) ? (m.p + 1) : (m.p + 1) * (m.p + 1);
+  if (adj) m.Yc.assign((size_t)ne * nf * 4 * NFd * B, 0.0);
   int bad_face = 0;
 
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : bad_face)
@@ -495,25 +513,40 @@ int mesh_build(Mesh& m, std::string& err) {
             for (int l = 0; l < dim; ++l) s2 += nrm[iq][k] * Dp[k * dim + l] * nrm[iq][l];
           sp[iq] = 0.5 * alpha * s2;
         }
-        double* Y = &m.Y[(size_t)(base + slot_of[i]) * 4 * B * B];
-        for (int a = 0; a < B; ++a)
-          for (int b = 0; b < B; ++b) {
-            double yee = 0.0, yen = 0.0, yne = 0.0, ynn = 0.0;
-            for (int iq = 0; iq < Qf; ++iq) {
-              const double w = wdS[iq], s2 = sp[iq];
-              const double pa = PHP[iq * B + a], pb = PHP[iq * B + b];
-              const double ma = PHM[iq * B + a], mb = PHM[iq * B + b];
-              const double fa = FLP[iq * B + a], fb = FLP[iq * B + b];
-              yee += w * (-0.5 * pa * fb - 0.5 * pb * fa + s2 * pa * pb);
-              yen += w * (0.5 * mb * fa - s2 * pa * mb);
-              yne += w * (0.5 * ma * fb - s2 * ma * pb);
-              ynn += w * (s2 * ma * mb);
-            }
-            Y[0 * B * B + a * B + b] = yee;
-            Y[1 * B * B + a * B + b] = yen;
-            Y[2 * B * B + a * B + b] = yne;
-            Y[3 * B * B + a * B + b] = ynn;
+        // only the entries a GLL nodal basis can make nonzero (a trace factor
+        // vanishes off the face): ee on e's face rows / face columns, en on
+        // n's face columns, ne on n's face rows, nn on both (layout in setup.h)
+        auto yent = [&](int part, int a, int b) {
+          double y = 0.0;
+          for (int iq = 0; iq < Qf; ++iq) {
+            const double w = wdS[iq], s2 = sp[iq];
+            const double pa = PHP[iq * B + a], pb = PHP[iq * B + b];
+            const double ma = PHM[iq * B + a], mb = PHM[iq * B + b];
+            const double fa = FLP[iq * B + a], fb = FLP[iq * B + b];
+            if (part == 0) y += w * (-0.5 * pa * fb - 0.5 * pb * fa + s2 * pa * pb);
+            else if (part == 1) y += w * (0.5 * mb * fa - s2 * pa * mb);
+            else if (part == 2) y += w * (0.5 * ma * fb - s2 * ma * pb);
+            else y += w * (s2 * ma * mb);
           }
+          return y;
+        };
+        const int NF = NFd, N1 = m.p + 1;
+        double* Y = &m.Yc[((size_t)e * nf + f) * 4 * NF * B];
+        double* yR = Y;                                  // NF x B
+        double* yC = yR + NF * B;                        // (B - NF) x NF
+        double* yEN = yC + (B - NF) * NF;                // B x NF
+        double* yNE = yEN + B * NF;                      // NF x B
+        double* yNN = yNE + NF * B;                      // NF x NF
+        for (int r = 0; r < NF; ++r)
+          for (int c = 0; c < B; ++c) yR[r * B + c] = yent(0, face_dof(dim, N1, f, r), c);
+        for (int r = 0; r < B - NF; ++r)
+          for (int c = 0; c < NF; ++c) yC[r * NF + c] = yent(0, off_dof(dim, N1, f, r), face_dof(dim, N1, f, c));
+        for (int r = 0; r < B; ++r)
+          for (int c = 0; c < NF; ++c) yEN[r * NF + c] = yent(1, r, face_dof(dim, N1, fn, c));
+        for (int r = 0; r < NF; ++r)
+          for (int c = 0; c < B; ++c) yNE[r * B + c] = yent(2, face_dof(dim, N1, fn, r), c);
+        for (int r = 0; r < NF; ++r)
+          for (int c = 0; c < NF; ++c) yNN[r * NF + c] = yent(3, face_dof(dim, N1, fn, r), face_dof(dim, N1, fn, c));
       }
       for (int a = 0; a < B; ++a)
         for (int b = 0; b < B; ++b) {
@@ -869,26 +902,7 @@ static int matrix_free_build_3d(const Mesh& m, const std::vector<int64_t>& perm,
 }
 
 
-// ---------------------------------------------------------------- face-structured operator
-namespace {
-int axis_stride(int N, int a) { return a == 0 ? 1 : (a == 1 ? N : N * N); }
-// r-th DoF on local face f (r = j1 + N j2 over the tangential axes in increasing order)
-int face_dof(int dim, int N, int f, int r) {
-  const int k = f / 2, s = f % 2;
-  int t[2] = {0, 0}, no = 0;
-  for (int a = 0; a < dim; ++a)
-    if (a != k) t[no++] = a;
-  int idx = s * (N - 1) * axis_stride(N, k) + (r % N) * axis_stride(N, t[0]);
-  if (dim == 3) idx += (r / N) * axis_stride(N, t[1]);
-  return idx;
-}
-// r-th DoF off local face f (r = j1 + N j2 + NF i', i' the normal index with
-// the face layer left out)
-int off_dof(int dim, int N, int f, int r) {
-  const int k = f / 2, s = f % 2, NF = dim == 2 ? N : N * N;
-  return (r / NF + 1 - s) * axis_stride(N, k) + face_dof(dim, N, 2 * k, r % NF);
-}
-}  // namespace
+
 
 int face_blocks_build(const Mesh& m, const HostLevel& l0, FaceBlocks& out, std::string& err) {
   const int dim = m.dim, B = m.B, N = m.p + 1, nf = 2 * dim;
@@ -940,6 +954,34 @@ int face_blocks_build(const Mesh& m, const HostLevel& l0, FaceBlocks& out, std::
     return AGG_EINVAL;
   }
   return AGG_OK;
+}
+
+
+void adjoint_face_parts_full(const Mesh& m, double* out) {
+  const int dim = m.dim, B = m.B, N = m.p + 1, nf = 2 * dim;
+  const int NF = dim == 2 ? N : N * N;
+  std::fill(out, out + (size_t)m.A.nnzb() * 4 * B * B, 0.0);
+  for (int64_t e = 0; e < m.ne; ++e)
+    for (int f = 0; f < nf; ++f) {
+      const int64_t rec = m.face_nbr[e * nf + f];
+      if (rec < 0) continue;
+      const int fn = (int)(rec % nf);
+      const double* Y = &m.Yc[((size_t)e * nf + f) * 4 * NF * B];
+      const double *yR = Y, *yC = yR + NF * B, *yEN = yC + (B - NF) * NF, *yNE = yEN + B * NF,
+                   *yNN = yNE + NF * B;
+      double* o = out + (size_t)(m.A.rowptr[e] + m.face_slot[e * nf + f]) * 4 * B * B;
+      double *ee = o, *en = o + B * B, *nee = o + 2 * B * B, *nn = o + 3 * B * B;
+      for (int r = 0; r < NF; ++r)
+        for (int c = 0; c < B; ++c) ee[face_dof(dim, N, f, r) * B + c] = yR[r * B + c];
+      for (int r = 0; r < B - NF; ++r)
+        for (int c = 0; c < NF; ++c) ee[off_dof(dim, N, f, r) * B + face_dof(dim, N, f, c)] = yC[r * NF + c];
+      for (int r = 0; r < B; ++r)
+        for (int c = 0; c < NF; ++c) en[r * B + face_dof(dim, N, fn, c)] = yEN[r * NF + c];
+      for (int r = 0; r < NF; ++r)
+        for (int c = 0; c < B; ++c) nee[face_dof(dim, N, fn, r) * B + c] = yNE[r * B + c];
+      for (int r = 0; r < NF; ++r)
+        for (int c = 0; c < NF; ++c) nn[face_dof(dim, N, fn, r) * B + face_dof(dim, N, fn, c)] = yNN[r * NF + c];
+    }
 }
 
 }  // namespace aggmg
