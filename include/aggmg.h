@@ -327,7 +327,7 @@ agg_status agg_monodomain_destroy(agg_sim_t sim);
  * work buffers (valid after any solve or V-cycle) on `stream`, so a caller
  * can time it with events; agg_kernel_cost gives its algorithmic HBM bytes
  * (every matrix, block and vector entry read or written once) and flops per
- * launch. */
+ * launch. Kernels 1-3 need n_levels >= 2 (else AGG_EUNSUPPORTED). */
 agg_status agg_profile_kernel(agg_hier_t hier, int kernel, int reps, void* stream);
 agg_status agg_kernel_cost(agg_hier_t hier, int kernel, double* bytes, double* flops);
 

@@ -216,7 +216,6 @@ agg_status agg_mg_hierarchy_setup(agg_mesh_t mesh, double mass_coeff, const agg_
   if (!mesh || !out) return fail(AGG_EINVAL, "NULL argument");
   agg_status chk = check_mg_opts(o, mass_coeff);
   if (chk) return chk;
-  if (o->n_levels < 2) return fail(AGG_EUNSUPPORTED, "the device solver needs n_levels >= 2");
   const Mesh& m = mesh->m;
   std::unique_ptr<agg_hier> h(new agg_hier());
   h->mesh = mesh;
@@ -489,7 +488,9 @@ agg_status agg_profile_kernel(agg_hier_t h, int kernel, int reps, void* stream) 
 
 agg_status agg_kernel_cost(agg_hier_t h, int kernel, double* bytes, double* flops) {
   if (!h || !bytes || !flops) return fail(AGG_EINVAL, "NULL argument");
-  if (h->eng->kernel_cost(kernel, *bytes, *flops)) return fail(AGG_EINVAL, "unknown kernel id");
+  const int rc = h->eng->kernel_cost(kernel, *bytes, *flops);
+  if (rc == AGG_EUNSUPPORTED) return fail(AGG_EUNSUPPORTED, "kernels 1-3 need n_levels >= 2");
+  if (rc) return fail(AGG_EINVAL, "unknown kernel id");
   return AGG_OK;
 }
 

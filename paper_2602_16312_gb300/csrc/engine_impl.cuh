@@ -884,6 +884,7 @@ class Engine : public EngineBase {
   }
 
   int kernel_loop(int id, int reps, cudaStream_t s, std::string& err) override {
+    if (id >= 1 && nlev_ < 2) { err = "kernels 1-3 need a smoothed level 0 (n_levels >= 2)"; return AGG_EUNSUPPORTED; }
     Lev& v = lev_[0];
     const int64_t n = v.nsl;
     for (int i = 0; i < reps; ++i) {
@@ -916,6 +917,7 @@ class Engine : public EngineBase {
   }
 
   int kernel_cost(int id, double& bytes, double& flops) const override {
+    if (id >= 1 && nlev_ < 2) return AGG_EUNSUPPORTED;
     const double n0 = (double)lev_[0].n, N = n0 * B, bb = (double)B * B;
     const double sT = sizeof(T), sD = sizeof(TD);
     const double bd = (B <= 32) ? (double)SymPad<TD, B>::NP : bb;   // stored smoother entries
