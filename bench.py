@@ -94,6 +94,20 @@ def rtree_m(args):
     return args.max_entries if args.agglomeration == "rtree" else 0
 
 
+def aggregate_over_ranks(t_local, steps, world, device):
+    """Whole-job throughput of `world` independent replicas, each of which
+    timed `steps` steps in t_local seconds: the slowest rank's time (an
+    all-reduce MAX over the process group) and steps * world over it."""
+    t = t_local
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return t, steps * world / t
+
+
 def workload_name(wl):
     cells = "quads" if wl.mesh.dim == 2 else "hexes"
     model = ("FHN", "Aliev-Panfilov", "Bueno-Orovio")[wl.ionic["model"]]
@@ -263,13 +277,8 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    t = ev0.elapsed_time(ev1) / 1e3
-    if world > 1:
-        tt = torch.tensor([t], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t, value = aggregate_over_ranks(ev0.elapsed_time(ev1) / 1e3, args.steps, world, dev)
     total_steps = args.steps * world
-    value = total_steps / t
     # ---- end to end through the public API with pinned host state: the same
     # time steps as the timed region, rerun from its starting state
     if args.e2e_steps is None:
