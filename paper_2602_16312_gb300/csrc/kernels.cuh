@@ -63,26 +63,42 @@ template <> __device__ __forceinline__ void unpack<__nv_bfloat16>(const uint4& v
   }
 }
 
+// Loads of data that one launch reads exactly once (operator blocks, smoother
+// blocks, quadrature data). With AGG_STREAM_LOADS they carry the streaming
+// (evict-first) cache hint, so that the L2 keeps the vectors, which the
+// neighbouring units read again, and the small coarse-level operators.
+#ifndef AGG_STREAM_LOADS
+#define AGG_STREAM_LOADS 1
+#endif
+template <typename V>
+__device__ __forceinline__ V ld_once(const V* p) {
+#if AGG_STREAM_LOADS
+  return __ldcs(p);
+#else
+  return __ldg(p);
+#endif
+}
+
 // Loads chunk `ch` of a sliced block into vals[0..VW) as the accumulation type A.
 template <typename TS, typename A> struct ChunkLoad;
 template <> struct ChunkLoad<double, double> {
   static constexpr int VW = 2;
   __device__ __forceinline__ static void load(const double* base, int ch, int lane, double* v) {
-    double2 t = __ldg(reinterpret_cast<const double2*>(base) + (size_t)ch * SL + lane);
+    double2 t = ld_once(reinterpret_cast<const double2*>(base) + (size_t)ch * SL + lane);
     v[0] = t.x; v[1] = t.y;
   }
 };
 template <> struct ChunkLoad<float, float> {
   static constexpr int VW = 4;
   __device__ __forceinline__ static void load(const float* base, int ch, int lane, float* v) {
-    float4 t = __ldg(reinterpret_cast<const float4*>(base) + (size_t)ch * SL + lane);
+    float4 t = ld_once(reinterpret_cast<const float4*>(base) + (size_t)ch * SL + lane);
     v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
   }
 };
 template <> struct ChunkLoad<__nv_bfloat16, float> {
   static constexpr int VW = 8;
   __device__ __forceinline__ static void load(const __nv_bfloat16* base, int ch, int lane, float* v) {
-    uint4 t = __ldg(reinterpret_cast<const uint4*>(base) + (size_t)ch * SL + lane);
+    uint4 t = ld_once(reinterpret_cast<const uint4*>(base) + (size_t)ch * SL + lane);
     unpack<__nv_bfloat16>(t, v);
   }
 };

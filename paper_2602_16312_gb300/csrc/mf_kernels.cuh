@@ -105,8 +105,8 @@ struct MfOp {
             g1 += T.D[b][l] * su;
           }
           const int iq = k + Q * l;
-          const float G00 = __ldg(cd + (iq * 4 + 0) * SL), G01 = __ldg(cd + (iq * 4 + 1) * SL);
-          const float G11 = __ldg(cd + (iq * 4 + 2) * SL), mm = __ldg(cd + (iq * 4 + 3) * SL);
+          const float G00 = ld_once(cd + (iq * 4 + 0) * SL), G01 = ld_once(cd + (iq * 4 + 1) * SL);
+          const float G11 = ld_once(cd + (iq * 4 + 2) * SL), mm = ld_once(cd + (iq * 4 + 3) * SL);
           const float w0 = G00 * g0 + G01 * g1;
           const float w1 = G01 * g0 + G11 * g1;
           const float wm = mm * uq;
@@ -151,8 +151,8 @@ struct MfOp {
           g1 += T.D[b][l] * tu[b][k];
         }
         const int iq = k + Q * l;
-        const float G00 = __ldg(cd + (iq * 4 + 0) * SL), G01 = __ldg(cd + (iq * 4 + 1) * SL);
-        const float G11 = __ldg(cd + (iq * 4 + 2) * SL), mm = __ldg(cd + (iq * 4 + 3) * SL);
+        const float G00 = ld_once(cd + (iq * 4 + 0) * SL), G01 = ld_once(cd + (iq * 4 + 1) * SL);
+        const float G11 = ld_once(cd + (iq * 4 + 2) * SL), mm = ld_once(cd + (iq * 4 + 3) * SL);
         const float w0 = G00 * g0 + G01 * g1;
         const float w1 = G01 * g0 + G11 * g1;
         const float wm = mm * uq;
@@ -215,9 +215,9 @@ struct MfOp {
         }
         const float g0p = (KF == 0) ? gn : gt;
         const float g1p = (KF == 0) ? gt : gn;
-        const float a0 = __ldg(fd + (q * 5 + 0) * SL), a1 = __ldg(fd + (q * 5 + 1) * SL);
-        const float b0 = __ldg(fd + (q * 5 + 2) * SL), b1 = __ldg(fd + (q * 5 + 3) * SL);
-        const float sq = __ldg(fd + (q * 5 + 4) * SL);
+        const float a0 = ld_once(fd + (q * 5 + 0) * SL), a1 = ld_once(fd + (q * 5 + 1) * SL);
+        const float b0 = ld_once(fd + (q * 5 + 2) * SL), b1 = ld_once(fd + (q * 5 + 3) * SL);
+        const float sq = ld_once(fd + (q * 5 + 4) * SL);
         const float um = rev ? un[Q - 1 - q] : un[q];
         const float h0 = rev ? gn0[Q - 1 - q] : gn0[q];
         const float h1 = rev ? gn1[Q - 1 - q] : gn1[q];
@@ -332,9 +332,9 @@ struct MfOp3 {
             g2 += T.L[b][l] * tw[b][k];
           }
           const float* gq = cd + (size_t)((k + Q * l + QQ * m) * 7) * SL;
-          const float G00 = __ldg(gq), G01 = __ldg(gq + SL), G02 = __ldg(gq + 2 * SL);
-          const float G11 = __ldg(gq + 3 * SL), G12 = __ldg(gq + 4 * SL), G22 = __ldg(gq + 5 * SL);
-          const float mm = __ldg(gq + 6 * SL);
+          const float G00 = ld_once(gq), G01 = ld_once(gq + SL), G02 = ld_once(gq + 2 * SL);
+          const float G11 = ld_once(gq + 3 * SL), G12 = ld_once(gq + 4 * SL), G22 = ld_once(gq + 5 * SL);
+          const float mm = ld_once(gq + 6 * SL);
           const float w0 = G00 * g0 + G01 * g1 + G02 * g2;
           const float w1 = G01 * g0 + G11 * g1 + G12 * g2;
           const float w2 = G02 * g0 + G12 * g1 + G22 * g2;
@@ -402,9 +402,9 @@ struct MfOp3 {
             hn += T.L[j2][q2] * nN[j2][q1];
           }
           const float* fq = fd + (size_t)((q1 + Q * q2) * 7) * SL;
-          const float aN = __ldg(fq), aT0 = __ldg(fq + SL), aT1 = __ldg(fq + 2 * SL);
-          const float bN = __ldg(fq + 3 * SL), bT0 = __ldg(fq + 4 * SL), bT1 = __ldg(fq + 5 * SL);
-          const float sq = __ldg(fq + 6 * SL);
+          const float aN = ld_once(fq), aT0 = ld_once(fq + SL), aT1 = ld_once(fq + 2 * SL);
+          const float bN = ld_once(fq + 3 * SL), bT0 = ld_once(fq + 4 * SL), bT1 = ld_once(fq + 5 * SL);
+          const float sq = ld_once(fq + 6 * SL);
           const float flux = aN * gnn + aT0 * gt0 + aT1 * gt1 + bN * hn + bT0 * ht0 + bT1 * ht1;
           const float jump = up - um;
           const float cf = -0.5f * flux + sq * jump;
