@@ -76,7 +76,7 @@ WORKLOADS = {
 # operator, agglomeration, kernel id) -> (bytes, summary). Other
 # configurations report null.
 NCU_TRAFFIC = {
-    ("jsquare2d_q2_512x512", "f32", "mf", "blocks", 1): (247.04e6, "profiles/k_cheb_mf_jsquare2d_q2_512.md"),
+    ("jsquare2d_q2_512x512", "f32", "mf", "blocks", 1): (238.97e6, "profiles/k_cheb_mf_jsquare2d_q2_512.md"),
 }
 
 

@@ -340,7 +340,7 @@ class Engine : public EngineBase {
     k_resid_restrict<T, B, Op><<<g, NTB, 0, s>>>(op, v.P, v.rhs, xo, v.S, st_);
     k_segsum<T, B><<<cdiv(c.n * B, 256), 256, 0, s>>>(c.child_ptr, v.S, c.rhs, c.n, st_);
     T* ec = vc(l + 1, s);
-    k_prolong<T, B><<<g, NTB, 0, s>>>(v.P, v.parent, ec, xo, v.nsl, st_);
+    k_prolong<T, B, OpStreams<Op>::value><<<g, NTB, 0, s>>>(v.P, v.parent, ec, xo, v.nsl, st_);
     k_cheb<T, TD, B, 1, Op><<<g, NTB, 0, s>>>(op, v.Dinv, v.rhs, xo, xn, v.d, T(0), v.c2[0], v.nsl, st_);
     std::swap(xo, xn);
     for (int k = 1; k < degree_; ++k) {

@@ -64,41 +64,43 @@ template <> __device__ __forceinline__ void unpack<__nv_bfloat16>(const uint4& v
 }
 
 // Loads of data that one launch reads exactly once (operator blocks, smoother
-// blocks, quadrature data). With AGG_STREAM_LOADS they carry the streaming
-// (evict-first) cache hint, so that the L2 keeps the vectors, which the
-// neighbouring units read again, and the small coarse-level operators.
+// and transfer blocks, quadrature data). On level 0 (ST, the default) they
+// carry the streaming (evict-first) cache hint, so that the L2 keeps the
+// vectors, which the neighbouring units read again, and the coarse levels'
+// data. Coarse-level blocks (ST = false) take the plain read-only path: the
+// smaller coarse levels then stay in L2 from one launch to the next.
 #ifndef AGG_STREAM_LOADS
 #define AGG_STREAM_LOADS 1
 #endif
-template <typename V>
+template <bool ST = true, typename V>
 __device__ __forceinline__ V ld_once(const V* p) {
-#if AGG_STREAM_LOADS
-  return __ldcs(p);
-#else
-  return __ldg(p);
-#endif
+  if constexpr (ST && AGG_STREAM_LOADS) return __ldcs(p);
+  else return __ldg(p);
 }
 
 // Loads chunk `ch` of a sliced block into vals[0..VW) as the accumulation type A.
 template <typename TS, typename A> struct ChunkLoad;
 template <> struct ChunkLoad<double, double> {
   static constexpr int VW = 2;
+  template <bool ST = true>
   __device__ __forceinline__ static void load(const double* base, int ch, int lane, double* v) {
-    double2 t = ld_once(reinterpret_cast<const double2*>(base) + (size_t)ch * SL + lane);
+    double2 t = ld_once<ST>(reinterpret_cast<const double2*>(base) + (size_t)ch * SL + lane);
     v[0] = t.x; v[1] = t.y;
   }
 };
 template <> struct ChunkLoad<float, float> {
   static constexpr int VW = 4;
+  template <bool ST = true>
   __device__ __forceinline__ static void load(const float* base, int ch, int lane, float* v) {
-    float4 t = ld_once(reinterpret_cast<const float4*>(base) + (size_t)ch * SL + lane);
+    float4 t = ld_once<ST>(reinterpret_cast<const float4*>(base) + (size_t)ch * SL + lane);
     v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
   }
 };
 template <> struct ChunkLoad<__nv_bfloat16, float> {
   static constexpr int VW = 8;
+  template <bool ST = true>
   __device__ __forceinline__ static void load(const __nv_bfloat16* base, int ch, int lane, float* v) {
-    uint4 t = ld_once(reinterpret_cast<const uint4*>(base) + (size_t)ch * SL + lane);
+    uint4 t = ld_once<ST>(reinterpret_cast<const uint4*>(base) + (size_t)ch * SL + lane);
     unpack<__nv_bfloat16>(t, v);
   }
 };
@@ -107,6 +109,14 @@ template <> struct ChunkLoad<__nv_bfloat16, float> {
 // per-thread vectors are staged in shared memory.
 template <int B> struct UnitThreads {
   static constexpr int value = (B > 32) ? 64 : 128;
+};
+
+// Whether the kernels of an operator load its blocks, the smoother blocks and
+// the transfer blocks with the streaming hint (see ld_once): true for the
+// level-0 operators; the coarse-level block-sparse operator specialises it
+// to false.
+template <typename Op> struct OpStreams {
+  static constexpr bool value = true;
 };
 
 // Minimum resident blocks per SM asked of the compiler for the kernels that
@@ -123,7 +133,7 @@ template <typename Op> struct OpMinBlocks<Op, std::void_t<decltype(Op::kMinBlock
 // acc[r] += sum_c M[r][c] x[c*XS] for one sliced block M (storage TS, math
 // A). x may be a register array (XS = 1, fully unrolled indices), a global
 // pointer (neighbour blocks, read through L1) or a strided shared-memory slot.
-template <typename TS, typename A, int B, int XS = 1>
+template <typename TS, typename A, int B, int XS = 1, bool ST = true>
 __device__ __forceinline__ void block_mv(const TS* base, int lane, const A* x, A* acc) {
   constexpr int VW = ChunkLoad<TS, A>::VW;
   constexpr int NCH = (B * B + VW - 1) / VW;
@@ -137,7 +147,7 @@ __device__ __forceinline__ void block_mv(const TS* base, int lane, const A* x, A
 #pragma unroll
       for (int rr = 0; rr < B / VW; ++rr) {
         A v[VW];
-        ChunkLoad<TS, A>::load(base, c * (B / VW) + rr, lane, v);
+        ChunkLoad<TS, A>::template load<ST>(base, c * (B / VW) + rr, lane, v);
 #pragma unroll
         for (int t = 0; t < VW; ++t) acc[rr * VW + t] += v[t] * xc;
       }
@@ -147,7 +157,7 @@ __device__ __forceinline__ void block_mv(const TS* base, int lane, const A* x, A
 #pragma unroll
   for (int ch = 0; ch < NCH; ++ch) {
     A v[VW];
-    ChunkLoad<TS, A>::load(base, ch, lane, v);
+    ChunkLoad<TS, A>::template load<ST>(base, ch, lane, v);
 #pragma unroll
     for (int t = 0; t < VW; ++t) {
       const int k = ch * VW + t;
@@ -156,14 +166,14 @@ __device__ __forceinline__ void block_mv(const TS* base, int lane, const A* x, A
   }
 }
 // acc[c] += sum_r M[r][c] x[r*XS] (transposed block)
-template <typename TS, typename A, int B, int XS = 1>
+template <typename TS, typename A, int B, int XS = 1, bool ST = true>
 __device__ __forceinline__ void block_mtv(const TS* base, int lane, const A* x, A* acc) {
   constexpr int VW = ChunkLoad<TS, A>::VW;
   constexpr int NCH = (B * B + VW - 1) / VW;
 #pragma unroll
   for (int ch = 0; ch < NCH; ++ch) {
     A v[VW];
-    ChunkLoad<TS, A>::load(base, ch, lane, v);
+    ChunkLoad<TS, A>::template load<ST>(base, ch, lane, v);
 #pragma unroll
     for (int t = 0; t < VW; ++t) {
       const int k = ch * VW + t;
@@ -174,7 +184,7 @@ __device__ __forceinline__ void block_mtv(const TS* base, int lane, const A* x, 
 
 // out[c] = sum_r M[r][c] x[r] for large blocks (B > 32): x in registers,
 // one output at a time through a pointer
-template <typename TS, typename A, int B>
+template <typename TS, typename A, int B, bool ST = true>
 __device__ __forceinline__ void block_mtv_out(const TS* base, int lane, const A* x, A* out) {
   constexpr int VW = ChunkLoad<TS, A>::VW;
   static_assert(B % VW == 0, "column-aligned chunks");
@@ -184,7 +194,7 @@ __device__ __forceinline__ void block_mtv_out(const TS* base, int lane, const A*
 #pragma unroll
     for (int rr = 0; rr < B / VW; ++rr) {
       A v[VW];
-      ChunkLoad<TS, A>::load(base, c * (B / VW) + rr, lane, v);
+      ChunkLoad<TS, A>::template load<ST>(base, c * (B / VW) + rr, lane, v);
 #pragma unroll
       for (int t = 0; t < VW; ++t) s += v[t] * x[rr * VW + t];
     }
@@ -207,7 +217,7 @@ template <typename TS, int B> struct DinvPad {
 };
 
 // acc += M x for one packed symmetric sliced block (x a register array)
-template <typename TS, typename A, int B>
+template <typename TS, typename A, int B, bool ST = true>
 __device__ __forceinline__ void sym_block_mv(const TS* base, int lane, const A* x, A* acc) {
   constexpr int VW = ChunkLoad<TS, A>::VW;
   A v[VW];
@@ -216,7 +226,7 @@ __device__ __forceinline__ void sym_block_mv(const TS* base, int lane, const A* 
 #pragma unroll
     for (int i = 0; i <= j; ++i) {
       const int k = j * (j + 1) / 2 + i;
-      if (k % VW == 0) ChunkLoad<TS, A>::load(base, k / VW, lane, v);
+      if (k % VW == 0) ChunkLoad<TS, A>::template load<ST>(base, k / VW, lane, v);
       const A m = v[k % VW];
       acc[i] += m * x[j];
       if (i != j) acc[j] += m * x[i];
@@ -259,7 +269,7 @@ __device__ __forceinline__ void sell_row(const SellView<T>& A, int64_t slice, in
   if constexpr (B > 32) {
     for (int j = s0; j < s1; ++j) {
       const int col = A.cols[(size_t)j * SL + lane];
-      block_mv<T, T, B>(A.vals + (size_t)j * SL * KP, lane, x + (size_t)col * B, acc);
+      block_mv<T, T, B, 1, false>(A.vals + (size_t)j * SL * KP, lane, x + (size_t)col * B, acc);
     }
     return;
   }
@@ -277,7 +287,7 @@ __device__ __forceinline__ void sell_row(const SellView<T>& A, int64_t slice, in
     }
 #pragma unroll
     for (int t = 0; t < PF; ++t)
-      if (t < ns) block_mv<T, T, B>(A.vals + (size_t)(j0 + t) * SL * KP, lane, xv[t], acc);
+      if (t < ns) block_mv<T, T, B, 1, false>(A.vals + (size_t)(j0 + t) * SL * KP, lane, xv[t], acc);
   }
 }
 
@@ -396,7 +406,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value, OpMinBlocks<Op>:
     __shared__ T tsh[B * NTB];
     T* ts = tsh + threadIdx.x;
     if (KIND == 0) {
-      block_mv<TD, T, B>(Db, lane, rhs + o, s);
+      block_mv<TD, T, B, 1, OpStreams<Op>::value>(Db, lane, rhs + o, s);
     } else {
       {
         T acc[B];
@@ -406,7 +416,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value, OpMinBlocks<Op>:
 #pragma unroll
         for (int r = 0; r < B; ++r) ts[r * NTB] = rhs[o + r] - acc[r];
       }
-      block_mv<TD, T, B, NTB>(Db, lane, ts, s);
+      block_mv<TD, T, B, NTB, OpStreams<Op>::value>(Db, lane, ts, s);
     }
   } else {
     T t[B];
@@ -421,7 +431,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value, OpMinBlocks<Op>:
 #pragma unroll
       for (int r = 0; r < B; ++r) t[r] = rhs[o + r] - acc[r];
     }
-    sym_block_mv<TD, T, B>(Db, lane, t, s);
+    sym_block_mv<TD, T, B, OpStreams<Op>::value>(Db, lane, t, s);
   }
 #pragma unroll
   for (int r = 0; r < B; ++r) {
@@ -458,7 +468,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value, OpMinBlocks<Op>:
     A.apply(slice, lane, x, acc);
 #pragma unroll
     for (int r = 0; r < B; ++r) acc[r] = rhs[o + r] - acc[r];
-    block_mtv_out<T, T, B>(Pb, lane, acc, S + o);
+    block_mtv_out<T, T, B, OpStreams<Op>::value>(Pb, lane, acc, S + o);
     return;
   } else {
     T acc[B];
@@ -468,7 +478,7 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value, OpMinBlocks<Op>:
     T t[B];
 #pragma unroll
     for (int r = 0; r < B; ++r) t[r] = rhs[o + r] - acc[r];
-    block_mtv<T, T, B>(Pb, lane, t, s);
+    block_mtv<T, T, B, 1, OpStreams<Op>::value>(Pb, lane, t, s);
   }
 #pragma unroll
   for (int j = 0; j < B; ++j) S[o + j] = s[j];
@@ -489,8 +499,8 @@ static __global__ void k_segsum(const int64_t* __restrict__ child_ptr, const T* 
   rc[id] = s;
 }
 
-// x_u += P_u e_{parent(u)}
-template <typename T, int B>
+// x_u += P_u e_{parent(u)}; ST: stream the P blocks (level 0)
+template <typename T, int B, bool ST = true>
 static __global__ void __launch_bounds__(UnitThreads<B>::value)
     k_prolong(const T* __restrict__ P, const int32_t* __restrict__ parent, const T* __restrict__ ec,
               T* __restrict__ x, int64_t nslices, const CGState* st) {
@@ -508,12 +518,12 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
 #pragma unroll
   for (int j = 0; j < B; ++j) acc[j] = T(0);
   if constexpr (B > 32) {
-    block_mv<T, T, B>(P + (size_t)slice * SL * KP, lane, eb, acc);
+    block_mv<T, T, B, 1, ST>(P + (size_t)slice * SL * KP, lane, eb, acc);
   } else {
     T ev[B];
 #pragma unroll
     for (int j = 0; j < B; ++j) ev[j] = eb[j];
-    block_mv<T, T, B>(P + (size_t)slice * SL * KP, lane, ev, acc);
+    block_mv<T, T, B, 1, ST>(P + (size_t)slice * SL * KP, lane, ev, acc);
   }
 #pragma unroll
   for (int r = 0; r < B; ++r) x[o + r] += acc[r];

@@ -500,6 +500,9 @@ struct SellOp {
     sell_row<T, B>(A, slice, lane, x, acc);
   }
 };
+template <typename T, int B> struct OpStreams<SellOp<T, B>> {
+  static constexpr bool value = false;
+};
 
 // y = op x for a unit-kernel operator (used to test an operator on its own)
 template <typename T, int B, typename Op>
