@@ -19,6 +19,7 @@ import resource
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -170,7 +171,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # the raw samples (kept for inspection; AGG_CLOCKS_DIR chooses the folder)
+        self.path = os.path.join(os.environ.get("AGG_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"aggmg_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
