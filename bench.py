@@ -222,9 +222,11 @@ def peaks():
         return {}
 
 
-# FP64 FMA throughput measured on this machine's GB300 (register-resident FMA
-# chains, 152 x 16 blocks x 256 threads): 0.600 TFMA/s = 1.20 TFLOP/s.
+# FP64 FMA throughput measured on a GB300 (register-resident FMA chains,
+# 152 x 16 blocks x 256 threads): 0.600 TFMA/s = 1.20 TFLOP/s.
 FP64_PEAK_GFLOPS = 1200.0
+# Nominal HBM3e bandwidth of a GB300, for context beside the measured copy rate.
+HBM_NOMINAL_GBS = 7900.0
 
 
 # ---------------------------------------------------------------- our arm
@@ -355,6 +357,8 @@ def run_ours(args, rank, world):
     else:
         roof = {"bound": "hbm", "achieved": kbytes / t_k / 1e9, "peak": hbm, "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    if roof["bound"] == "hbm":
+        roof["frac_of_nominal"] = roof["achieved"] / HBM_NOMINAL_GBS
     roof["traffic"] = None
     cap = NCU_TRAFFIC.get((wl.name, args.form, args.fine, args.agglomeration, kid))
     if cap is not None:
@@ -393,7 +397,8 @@ def run_ours(args, rank, world):
                    "levels": st["units"], "op_complexity": st["op_complexity"], "setup_s": setup_s,
                    "conditional_graph": os.environ.get("AGG_NO_COND_GRAPH") is None, "flexible_cg": flexible},
         "iterations": {"mean": float(np.mean(its)), "min": int(min(its)), "max": int(max(its)),
-                       "std": float(np.std(its)), "warmup": its_w},
+                       "std": float(np.std(its)), "warmup": its_w,
+                       "ms_per_pcg_iteration": 1e3 * t / max(1, int(np.sum(its)))},
         "e2e": {"value": args.e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": (u.numel() + w.numel()) * 8,
                 "d2h_bytes_per_step": (u.numel() + w.numel()) * 8, "steps": args.e2e_steps,
                 "same_steps_as_timed": args.e2e_steps == args.steps,
