@@ -327,7 +327,12 @@ agg_status agg_monodomain_destroy(agg_sim_t sim);
  * work buffers (valid after any solve or V-cycle) on `stream`, so a caller
  * can time it with events; agg_kernel_cost gives its algorithmic HBM bytes
  * (every matrix, block and vector entry read or written once) and flops per
- * launch. Kernels 1-3 need n_levels >= 2 (else AGG_EUNSUPPORTED). */
+ * launch. Kernels 1-3 need n_levels >= 2 (else AGG_EUNSUPPORTED).
+ * agg_kernel_cost also takes id 4: one iteration of the solve body (float64
+ * SpMV, CG update, one V-cycle over every level, z and p updates), the sum
+ * of its launches' algorithmic bytes and flops, counting the float32 copy of
+ * r and the flexible (r, z_old) read in the reduced-precision forms;
+ * agg_profile_kernel rejects it (AGG_EINVAL). */
 agg_status agg_profile_kernel(agg_hier_t hier, int kernel, int reps, void* stream);
 agg_status agg_kernel_cost(agg_hier_t hier, int kernel, double* bytes, double* flops);
 

@@ -936,9 +936,59 @@ class Engine : public EngineBase {
         flops = 2 * fe + 2 * n0 * bb + N;
         break;
       case 3: bytes = n0 * bb * sT + 2 * N * sT + (double)lev_[1].n * B * sT + n0 * 4; flops = 2 * n0 * bb + N; break;
+      case 4: iteration_cost(bytes, flops); break;
       default: return AGG_EINVAL;
     }
     return AGG_OK;
+  }
+
+  // Algorithmic bytes and flops of one iteration of the solve body: the
+  // float64 SpMV, the CG update, one V-cycle over every level, the z and p
+  // updates. Each launch reads its operator, block and vector entries once
+  // and writes each output once; flops count two per stored matrix entry
+  // used (the matrix-free level-0 operator as its assembled counterpart).
+  void iteration_cost(double& bytes, double& flops) const {
+    const double bb = (double)B * B, sT = sizeof(T), sD = sizeof(TD);
+    const double n0 = (double)lev_[0].n, N = n0 * B, fe = face_entries_;
+    const double fidx = n0 * 2 * FaceShape<B>::D * 5.0;
+    const double deg = degree_;
+    // outer CG: SpMV (p in, q out), update (x, r, p, q in; x, r out; the
+    // float32 copy of r and the flexible (r, z_old) read in the reduced-
+    // precision forms), z = V(r) with (r, z), p = z + beta p
+    const bool lowp = !std::is_same<T, double>::value;
+    bytes = fe * 8 + fidx + 2 * N * 8;
+    bytes += 6 * N * 8 + (lowp ? N * 4 + N * 8 : 0.0);
+    bytes += N * sT + 2 * N * 8 + 3 * N * 8;
+    flops = 2 * fe + 12 * N;
+    for (int l = 0; l < nlev_; ++l) {
+      const double nl = (double)lev_[l].n, Nl = nl * B;
+      if (l == nlev_ - 1) {                                 // two dense triangular products
+        const double nc = (double)nc_;
+        bytes += 2 * nc * nc * 8 + 2 * nc * sT + 2 * nc * 8;
+        flops += 4 * nc * nc;
+        break;
+      }
+      const double Nc = (double)lev_[l + 1].n * B;
+      double op, opf, dinv;
+      if (l == 0) {
+        op = use_mf0() ? (double)mf_bytes_ : fe * sT + fidx;
+        opf = 2 * fe;
+        dinv = nl * ((B <= 32) ? (double)SymPad<TD, B>::NP : bb) * sD;
+      } else {
+        const double nz = (double)nnzb_[l];
+        op = nz * bb * sT + nz * 4 + (nl + 1) * 4;
+        opf = 2 * nz * bb;
+        dinv = nl * bb * sD;                                // full blocks on levels >= 1
+      }
+      const double P = nl * bb * sT;
+      // 2 deg smoother steps (2 deg - 1 with an operator product: the first
+      // step from x = 0 has none), residual + restriction, segmented sum,
+      // prolongation
+      bytes += 2 * deg * op + 2 * deg * dinv + 2 * P;
+      bytes += (3 + 2 * (deg - 1) * 5 + 4) * Nl * sT;      // smoother vectors
+      bytes += 3 * Nl * sT + (Nl + Nc) * sT + ((double)lev_[l + 1].n + 1) * 8 + (Nc + 2 * Nl) * sT + nl * 4;
+      flops += 2 * deg * opf + 2 * deg * 2 * nl * bb + 2 * 2 * nl * bb + 10 * deg * Nl;
+    }
   }
 
   int adjoint_step(const double* u_n, const double* w_n, const double* u_np1, double* ubar, double* wbar,
