@@ -95,3 +95,37 @@ def test_locate_points_reproduces_polynomials():
     vals = np.einsum("si,si->s", Wt, g(xn)[elem])
     np.testing.assert_allclose(vals, g(pts), atol=1e-12)
     del f
+
+
+@pytest.mark.parametrize("model", ["fhn", "ap"])
+def test_adjoint_step_is_the_transpose_of_the_step_linearisation(model):
+    """Dot-product test of one reverse step: with J the Jacobian of the
+    forward step (u^n, w^n) -> (u^{n+1}, w^{n+1}), taken here by central
+    differences of the forward step, <J v, y> equals <v, J^T y> where
+    J^T y = (ubar^n, wbar^n) is what adjoint_step returns for the seed y."""
+    mesh, D = _setup(dim=2, n=3, p=2, jit=0.15)
+    p = 2
+    disc = sipg.assemble(mesh.vertices, mesh.elements, D, p, 1, 10.0)
+    forms = sipg.attributed_forms(mesh.vertices, mesh.elements, D, p, 1, 10.0)
+    prm = dict(W.FHN) if model == "fhn" else dict(W.ALIEV_PANFILOV)
+    opts = omd.StepOptions(dt=0.05, ionic=prm, rtol=1e-14, iapp_value=1.0, iapp_steps=3)
+    hier = omg.build_hierarchy(disc, opts.mass_coeff(), [])      # one level: the solves are direct
+    rng = np.random.default_rng(12)
+    n = disc.n
+    u, w = rng.uniform(0.05, 0.9, n), rng.uniform(0.0, 0.3, n)
+    du, dw = rng.standard_normal(n), rng.standard_normal(n)
+    yu, yw = rng.standard_normal(n), rng.standard_normal(n)
+    mask = np.repeat((np.arange(mesh.n_elements) < 2).astype(float), disc.B)
+    h = 1e-5
+
+    def forward(s):
+        un, wn, _ = omd.step(disc, hier, opts, u + s * du, w + s * dw, mask, 0)
+        return un, wn
+
+    (up, wp), (um, wm) = forward(h), forward(-h)
+    lhs = (up - um) @ yu / (2 * h) + (wp - wm) @ yw / (2 * h)
+    u1, _ = forward(0.0)
+    ubar_n, wbar_n, _ = omd.adjoint_step(disc, hier, opts, forms, u, w, u1, yu, yw, rtol=1e-14)
+    rhs = du @ ubar_n + dw @ wbar_n
+    scale = np.abs(du) @ np.abs(ubar_n) + np.abs(dw) @ np.abs(wbar_n)
+    assert abs(lhs - rhs) <= 1e-8 * scale, (lhs, rhs)
