@@ -99,8 +99,11 @@ def volume_matrices(vertices, elements, D, p, quad_extra=1, chunk=32768):
         _, _, detJ, Jinv = _geometry(X, N, dN)
         G = _physical_gradients(Jinv, grad_hat)
         wJ = w[None, :] * detJ
-        Me[s:s + chunk] = np.einsum("eq,iq,jq->eij", wJ, phi, phi)
-        Ke[s:s + chunk] = np.einsum("eq,eqik,ekm,eqjm->eij", wJ, G, D[s:s + chunk], G)
+        Me[s:s + chunk] = np.einsum("eq,iq,jq->eij", wJ, phi, phi, optimize=True)
+        # the same sum, contracted in two steps: (D grad phi_j) first, then
+        # sum_q w |J| grad phi_i . (D grad phi_j)
+        DG = np.einsum("ekm,eqjm->eqjk", D[s:s + chunk], G)
+        Ke[s:s + chunk] = np.einsum("eq,eqik,eqjk->eij", wJ, G, DG, optimize=True)
         vol[s:s + chunk] = wJ.sum(axis=1)
     return Me, Ke, vol
 
@@ -244,10 +247,10 @@ def face_matrices(vertices, elements, D, p, volumes, c_pen, quad_extra=1, chunk=
         sgn = (1.0, -1.0)
         for si in range(2):
             for sj in range(2):
-                blk = (-0.5 * sgn[si] * np.einsum("fq,fqi,fqj->fij", wdS, phis[si], fluxes[sj])
-                       - 0.5 * sgn[sj] * np.einsum("fq,fqj,fqi->fij", wdS, phis[sj], fluxes[si])
+                blk = (-0.5 * sgn[si] * np.einsum("fq,fqi,fqj->fij", wdS, phis[si], fluxes[sj], optimize=True)
+                       - 0.5 * sgn[sj] * np.einsum("fq,fqj,fqi->fij", wdS, phis[sj], fluxes[si], optimize=True)
                        + sgn[si] * sgn[sj] * np.einsum("fq,fqi,fqj->fij", wdS * sigma,
-                                                       phis[si], phis[sj]))
+                                                       phis[si], phis[sj], optimize=True))
                 blocks[sl, si, sj] = blk
     return ep, em, blocks
 

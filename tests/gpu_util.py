@@ -14,7 +14,21 @@ def oracle_setup(wl, c=None):
 
 
 def rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    """Element-wise error of a against the reference b: max_i |a_i - b_i|
+    divided by max_i |b_i| (so one wrong entry among millions is not averaged
+    away, as it would be in a 2-norm ratio)."""
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    assert a.shape == b.shape, (a.shape, b.shape)
+    return float(np.abs(a - b).max(initial=0.0) / max(np.abs(b).max(initial=0.0), 1e-300))
+
+
+def worst(a, b):
+    """Index, value and reference of the largest element-wise difference (for messages)."""
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    i = int(np.argmax(np.abs(a - b)))
+    return dict(index=i, got=float(a[i]), ref=float(b[i]), err=rel(a, b))
 
 
 def step_opts(wl, rtol=None):
