@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=None,
                     help="steps of the end-to-end leg (default: --steps; it reruns the timed steps "
                          "from the same state)")
+    ap.add_argument("--fp64-steps", type=int, default=10,
+                    help="also time this many steps of the plain float64 form (float64 V-cycle) from the "
+                         "timed region's starting state, in the same run (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-kernel", type=int, default=None,
                     help="set up, launch kernel id K three times (for ncu) and exit")
@@ -72,13 +75,41 @@ WORKLOADS = {
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# dominant kernel, from one ncu capture of the same configuration and kernel
-# code, with the summary that records the command: (workload, form, level-0
-# operator, agglomeration, kernel id) -> (bytes, summary). Other
-# configurations report null.
-NCU_TRAFFIC = {
-    ("jsquare2d_q2_512x512", "f32", "mf", "blocks", 1): (238.97e6, "profiles/k_cheb_mf_jsquare2d_q2_512.md"),
-}
+# dominant kernel, from one ncu capture of the same configuration:
+# (workload, form, level-0 operator, agglomeration, kernel id) ->
+# (bytes, sha256 prefix of the kernel sources the capture ran). A stored figure
+# is reported only while the kernel sources still hash to the captured value;
+# after any change to them, and for other configurations, traffic is null.
+NCU_TRAFFIC = {}
+KERNEL_SOURCES = ("kernels.cuh", "mf_kernels.cuh", "face_op.cuh", "coarse_kernels.cuh", "cg_kernels.cuh")
+
+
+def kernel_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2602_16312_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def host_cpu():
+    """Logical CPUs available to this process and the CPU model (lscpu)."""
+    try:
+        n = len(os.sched_getaffinity(0))
+    except AttributeError:
+        n = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, timeout=10).stdout.decode()
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    import platform
+    return {"nproc": n, "model": model or platform.processor() or platform.machine(), "arch": platform.machine()}
 
 
 def workload_expr(args):
@@ -143,11 +174,13 @@ print(json.dumps(dict(t_step=t_step, iters=res.iterations)))
 """
 
 
-def cpu_oracle_sample(expr, rtree_M=0):
-    """Runs the oracle single-threaded in a fresh process: one full time step
-    (step 0: ionic update, RHS, PCG to 1e-8) of the benchmark workload, timed
-    on this host's cores; the oracle's set-up is not timed."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+def cpu_oracle_sample(expr, rtree_M=0, threads=1):
+    """Runs the oracle in a fresh process with `threads` BLAS/OpenMP threads:
+    one full time step (step 0: ionic update, RHS, PCG to 1e-8) of the
+    benchmark workload, timed on this host's cores; the oracle's set-up is not
+    timed."""
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
     out = subprocess.run([sys.executable, "-c", ORACLE_SNIPPET.format(root=ROOT, expr=expr, rtree_M=rtree_M)],
                          env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, timeout=1800)
     if out.returncode != 0:
@@ -155,11 +188,26 @@ def cpu_oracle_sample(expr, rtree_M=0):
     return json.loads(out.stdout.decode().strip().splitlines()[-1])
 
 
-def cpu_baseline_entry(sample, name):
-    return {"value": 1.0 / sample["t_step"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"oracle (numpy/scipy float64, 1 thread) on {name}: one full time "
-                       f"step (step 0: ionic update, RHS, PCG to 1e-8 in {sample['iters']} iterations) timed, "
-                       f"{sample['t_step']:.1f} s; oracle set-up excluded")}
+def cpu_baseline_samples(expr, rtree_M=0):
+    """The oracle timed with one thread and with every host CPU (BLAS/OpenMP
+    threads = nproc; the oracle's sparse products stay single-threaded)."""
+    cpu = host_cpu()
+    one = cpu_oracle_sample(expr, rtree_M, 1)
+    allc = cpu_oracle_sample(expr, rtree_M, cpu["nproc"]) if cpu["nproc"] > 1 else one
+    return {"one": one, "all": allc, "cpu": cpu}
+
+
+def cpu_baseline_entry(samples, name):
+    one, allc, cpu = samples["one"], samples["all"], samples["cpu"]
+    return {"value": 1.0 / allc["t_step"], "unit": UNIT, "cores": cpu["nproc"], "kind": "oracle",
+            "cpu_model": cpu["model"], "nproc": cpu["nproc"], "arch": cpu["arch"],
+            "single_thread": {"value": 1.0 / one["t_step"], "cores": 1, "t_step_s": one["t_step"]},
+            "all_cores": {"value": 1.0 / allc["t_step"], "cores": cpu["nproc"], "t_step_s": allc["t_step"]},
+            "sample": (f"oracle (numpy/scipy float64) on {name}: one full time step (step 0: ionic update, "
+                       f"RHS, PCG to 1e-8 in {one['iters']} iterations) timed in a fresh process, once with "
+                       f"1 thread ({one['t_step']:.1f} s) and once with BLAS/OpenMP threads = nproc = "
+                       f"{cpu['nproc']} ({allc['t_step']:.1f} s; value and cores are this run); "
+                       f"oracle set-up excluded")}
 
 
 # ---------------------------------------------------------------- clocks
@@ -237,7 +285,7 @@ def run_ours(args, rank, world):
 
     sample = None
     if rank == 0 and not args.no_cpu_baseline:
-        sample = cpu_oracle_sample(workload_expr(args), rtree_m(args))   # before any GPU work
+        sample = cpu_baseline_samples(workload_expr(args), rtree_m(args))   # before any GPU work
 
     from paper_2602_16312_gb300 import aggmg, build
     build.build()
@@ -308,6 +356,35 @@ def run_ours(args, rank, world):
     e2e_same = None
     if args.e2e_steps == args.steps:
         e2e_same = bool(torch.equal(uh.to(dev), u_end))     # bitwise: deterministic reductions
+    # ---- the plain float64 form (float64 V-cycle on the face-structured
+    # level-0 operator) from the same starting state, timed the same way, so
+    # one run shows both forms at the same 1e-8 relative residual
+    fp64 = None
+    if args.form != "f64" and args.fp64_steps > 0:
+        h64 = aggmg.Hierarchy(mesh, 1.0 / wl.dt, wl.maps, precision="f64", fine="bsr")
+        s64 = aggmg.Monodomain(h64, wl.dt, wl.ionic, iapp_mask=mask, iapp_value=wl.iapp_value,
+                               iapp_steps=wl.iapp_steps, rtol=wl.rtol, flexible=False)
+        u64, w64 = u_start.clone(), w_start.clone()
+        s64.set_clock(args.warmup)
+        s64.step(u64, w64, 1)                                  # warm-up (graph upload)
+        u64.copy_(u_start)
+        w64.copy_(w_start)
+        s64.set_clock(args.warmup)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        its64 = s64.step(u64, w64, args.fp64_steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t64 = ev0.elapsed_time(ev1) / 1e3
+        v64 = args.fp64_steps / t64
+        fp64 = {"value": v64, "unit": UNIT, "steps": args.fp64_steps, "ms_per_step": 1e3 * t64 / args.fp64_steps,
+                "mdof_per_s": N * args.fp64_steps / t64 / 1e6, "iterations_mean": float(np.mean(its64)),
+                "dtype": "f64 outer CG + f64 V-cycle", "fine_operator": "bsr",
+                "value_over_fp64": value / world / v64,
+                "note": "plain float64 form, steps warmup..warmup+steps from the timed region's starting state"}
+        s64.close()
+        h64.close()
+        del u64, w64
     # ---- reverse (adjoint) steps: K forward steps keep their states, then K
     # reverse steps from a seeded dL/du at the end accumulate the per-element
     # log-conductivity gradient (the adjoint form's per-step work)
@@ -374,8 +451,15 @@ def run_ours(args, rank, world):
         roof["frac_of_nominal"] = roof["achieved"] / HBM_NOMINAL_GBS
     roof["traffic"] = None
     cap = NCU_TRAFFIC.get((wl.name, args.form, args.fine, args.agglomeration, kid))
-    if cap is not None:
-        roof["traffic"], roof["traffic_source"] = cap
+    src_hash = kernel_sources_hash()
+    if cap is not None and cap[1] == src_hash:
+        roof["traffic"] = cap[0]
+        roof["traffic_source"] = (f"ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one launch) of "
+                                  f"this kernel and configuration, taken before this run on kernel sources "
+                                  f"{src_hash} (unchanged since)")
+    else:
+        roof["traffic_source"] = ("null: no ncu capture of this configuration with the current kernel sources "
+                                  f"({src_hash})")
     roof["kernel"] = KERNEL_NAMES_MF[kid] if args.fine == "mf" else KERNEL_NAMES[kid]
     roof["us_per_launch"] = t_k * 1e6
     roof["algorithmic_bytes"] = kbytes
@@ -402,11 +486,8 @@ def run_ours(args, rank, world):
                                      "bf16s": "f32 V-cycle with bf16-stored smoother blocks"}[args.form],
         "data": "synthetic",
         "mdof_per_s": N * total_steps / t / 1e6,
-        "config": {"workload": workload_name(wl), "form": args.form, "fine_operator": args.fine,
-                   "agglomeration": args.agglomeration if args.agglomeration == "blocks"
-                   else f"R*-tree, M = {args.max_entries}",
-                   "parallelism": f"replicas x{world}",
-                   "l2": f"inputs larger than L2 (fine float64 matrix {k0bytes / 1e9:.2f} GB, 129 MB L2)",
+        "config": bench_config(wl, args),
+        "solver": {"form": args.form, "fine_operator": args.fine, "parallelism": f"replicas x{world}",
                    "levels": st["units"], "op_complexity": st["op_complexity"], "setup_s": setup_s,
                    "conditional_graph": os.environ.get("AGG_NO_COND_GRAPH") is None, "flexible_cg": flexible},
         "iterations": {"mean": float(np.mean(its)), "min": int(min(its)), "max": int(max(its)),
@@ -421,6 +502,7 @@ def run_ours(args, rank, world):
         "clocks": clk.summary(),
         "host_peak_rss_gb": resource.getrusage(resource.RUSAGE_SELF).ru_maxrss / 2**20,
         **({"adjoint": adjoint} if adjoint is not None else {}),
+        **({"fp64_form": fp64} if fp64 is not None else {}),
     }
     if sample is not None:
         line["cpu_baseline"] = cpu_baseline_entry(sample, wl.name)
@@ -430,19 +512,92 @@ def run_ours(args, rank, world):
     hier.close()
 
 
+REF_SAMPLE_ITERS = 2
+
+
+def bench_config(wl, args):
+    """The workload the line is quoted on; identical in both arms."""
+    B = (wl.degree + 1) ** wl.mesh.dim
+    a0_gb = wl.mesh.n_elements * (2 * wl.mesh.dim + 1) * B * B * 8 / 1e9
+    return {"workload": workload_name(wl),
+            "agglomeration": args.agglomeration if args.agglomeration == "blocks"
+            else f"R*-tree, M = {args.max_entries}",
+            "start": f"from rest (u = w = 0), stimulus on for the first {wl.iapp_steps} steps; "
+                     f"{args.warmup} warm-up steps, then the timed steps",
+            "l2": (f"inputs larger than L2 (float64 fine operator ~{a0_gb:.2f} GB against 129 MB of L2), no flush"
+                   if a0_gb > 0.129 else "small case: inputs fit in L2, no flush")}
+
+
 def run_reference(args, rank):
-    """The oracle as it stands, on the host cores, as the reference arm."""
+    """The oracle as it stands, on the host cores, as the reference arm.
+
+    Set-up (assembly, Algorithm 3) is not timed. The first warm-up step is a
+    full oracle time step (ionic update, RHS, PCG to the workload's rtol),
+    which gives the iterations per step n_it; the other warm-up steps and
+    every timed step are bounded samples: the next oracle time step of the
+    same trajectory with its PCG stopped after REF_SAMPLE_ITERS iterations.
+    A sample and a full step both consist of the pointwise work plus one
+    (SpMV + V-cycle) pass per PCG iteration and one for the initial
+    residual, so a full step takes t_sample * (n_it + 1) / (REF_SAMPLE_ITERS
+    + 1); `value` is the time-steps/s this gives, `ms_per_step` the measured
+    time of a sample."""
     if rank != 0:
         return
-    sample = cpu_oracle_sample(workload_expr(args), rtree_m(args))
+    import numpy as np
+    from oracle import monodomain as md
+    from oracle import multigrid as mg
+    from oracle import sipg
+    from paper_2602_16312_gb300 import workloads as W
+    cpu = host_cpu()
     wl = workload(args)
-    base = cpu_baseline_entry(sample, wl.name)
-    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sample["t_step"],
+    if args.agglomeration == "rtree":
+        import dataclasses
+        from oracle import rtree
+        t = rtree.build(wl.mesh.vertices, wl.mesh.elements, args.max_entries)
+        wl = dataclasses.replace(wl, maps=rtree.agglomeration_maps(t, wl.mesh.n_elements, t.root.level + 1))
+    disc = sipg.assemble(wl.mesh.vertices, wl.mesh.elements, wl.conductivity, wl.degree, wl.penalty_mode,
+                         wl.penalty_coeff)
+    full = md.StepOptions(dt=wl.dt, ionic=wl.ionic, rtol=wl.rtol, iapp_value=wl.iapp_value,
+                          iapp_steps=wl.iapp_steps)
+    h = mg.build_hierarchy(disc, full.mass_coeff(), wl.maps)
+    u = np.zeros(disc.n)
+    w = np.repeat(W.resting_gates(wl.ionic)[:, None], disc.n, axis=1)
+    if w.shape[0] == 1:
+        w = w[0]
+    mask = wl.stim_mask_nodal()
+    t0 = time.perf_counter()
+    u, w, res = md.step(disc, h, full, u, w, mask, 0)
+    t_full = time.perf_counter() - t0
+    n_it = res.iterations
+    import dataclasses
+    sample = dataclasses.replace(full, max_it=REF_SAMPLE_ITERS)
+    for n in range(1, args.warmup):
+        u, w, _ = md.step(disc, h, sample, u, w, mask, n)
+    ts = []
+    first = max(args.warmup, 1)
+    for n in range(first, first + args.steps):
+        t0 = time.perf_counter()
+        u, w, _ = md.step(disc, h, sample, u, w, mask, n)
+        ts.append(time.perf_counter() - t0)
+    t_sample = float(np.mean(ts))
+    t_step = t_sample * (n_it + 1) / (REF_SAMPLE_ITERS + 1)
+    value = 1.0 / t_step
+    base = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": cpu["model"],
+            "nproc": cpu["nproc"], "arch": cpu["arch"],
+            "sample": (f"oracle (numpy/scipy float64, one process, one BLAS/OpenMP thread) on {wl.name}: "
+                       f"{args.steps} timed samples, each the next time step of the trajectory with PCG "
+                       f"stopped after {REF_SAMPLE_ITERS} iterations ({1e3 * t_sample:.0f} ms each), scaled "
+                       f"to a full step by (n_it + 1)/{REF_SAMPLE_ITERS + 1} with n_it = {n_it} from one "
+                       f"untimed full step ({t_full:.1f} s); oracle set-up excluded")}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_sample,
+            "ms_per_step_note": "measured time of one bounded sample; a full oracle time step is "
+                                f"{1e3 * t_step:.0f} ms (= 1 / value)",
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload_name(wl), "form": "oracle f64"},
+            "data": "synthetic", "config": bench_config(wl, args),
+            "solver": {"form": "oracle float64 (numpy/scipy)", "iterations_per_step": n_it},
             "cpu_baseline": base,
-            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -451,6 +606,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
+        # one BLAS/OpenMP thread, fixed before numpy loads: the line reports cores = 1
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[k] = "1"
         run_reference(args, rank)
         return
     if args.profile_kernel is not None:

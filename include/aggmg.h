@@ -193,10 +193,15 @@ agg_status agg_vcycle_apply(agg_hier_t hier, const double* r_dev, double* z_dev,
  * ((units rounded up to 32) * (p+1)^d) exceeds AGG_STATIC_APPLY_MAX_ENTRIES
  * returns AGG_EINVAL. The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress, once per device, with that device current);
- * make that first call before any stream capture. The array is shared by all
- * calls and keeps the last call's contents; nothing in it has to start at
- * zero (each call writes every entry it reads). Calls that overlap on the
- * GPU (two streams, or two threads) race on the array: order them on one
+ * make that first call before any stream capture. The address is kept for
+ * the life of the process, so resetting the device (cudaDeviceReset) or
+ * destroying its primary context after the first call is not supported
+ * while the library stays loaded. The array is shared by all calls and keeps
+ * the last call's contents; nothing in it has to start at zero: every entry
+ * that contributes to y is written earlier in the same call, and the padded
+ * lanes of the last 32-unit slice, which may read stale entries, only feed
+ * padded outputs that are never copied to y. Calls that overlap on the GPU
+ * (two streams, or two threads) race on the array: order them on one
  * stream. */
 #define AGG_STATIC_APPLY_MAX_ENTRIES (1LL << 20)
 agg_status agg_operator_apply_static(agg_hier_t hier, int level, const double* x_dev, double* y_dev,
