@@ -29,14 +29,27 @@ def _face_keys(elements, ids, dim):
     return np.concatenate(keys)
 
 
+_INC = {}
+
+
+def _incidence(elements):
+    """Vertex -> element incidence of a connectivity array (sorted vertex ids
+    and the flat positions they come from), cached per array."""
+    key = (elements.__array_interface__["data"][0], elements.shape)
+    if key not in _INC:
+        flat = elements.ravel()
+        order = np.argsort(flat, kind="stable")
+        _INC.clear()
+        _INC[key] = (order, flat[order])
+    return _INC[key]
+
+
 def face_neighbours(elements, chunk, dim):
     """The chunk's elements plus every element sharing a face (the same
     2^(d-1) corner vertices) with one of them, sorted."""
     chunk = np.asarray(chunk, dtype=np.int64)
     E, V = elements.shape
-    flat = elements.ravel()
-    order = np.argsort(flat, kind="stable")
-    sv = flat[order]
+    order, sv = _incidence(elements)
     verts = np.unique(elements[chunk].ravel())
     lo = np.searchsorted(sv, verts, side="left")
     hi = np.searchsorted(sv, verts, side="right")
