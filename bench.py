@@ -465,19 +465,35 @@ def run_ours(args, rank, world):
     roof["algorithmic_bytes"] = kbytes
     roof["peak_source"] = "MEASURED_PEAKS.json hbm_gbs (of measured)" if roof["bound"] == "hbm" else \
         "measured FP64 FMA rate on GB300 (of measured)"
+    # the float64 level-0 operator evaluated matrix-free (measured alternative
+    # to the face-structured product of the outer CG; same work counted)
+    mf64 = None
+    try:
+        hier.profile_kernel(5, 2)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        hier.profile_kernel(5, reps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_k5 = ev0.elapsed_time(ev1) / 1e3 / reps
+        k5bytes, k5flops = hier.kernel_cost(5)
+        mf64 = {"kernel": "k_spmv<double, MfOp<double>> (fine float64 operator, matrix-free)",
+                "us_per_launch": t_k5 * 1e6, "algorithmic_bytes": k5bytes,
+                "achieved_gflops_assembled_equivalent": k5flops / t_k5 / 1e9,
+                "achieved_gbs": k5bytes / t_k5 / 1e9, "time_over_face_structured": t_k5 / t_k0}
+    except aggmg.AggError:
+        pass
     other = {"kernel": KERNEL_NAMES[0], "us_per_launch": t_k0 * 1e6,
              "achieved_gflops": k0flops / t_k0 / 1e9, "fp64_peak_gflops": FP64_PEAK_GFLOPS,
              "frac_fp64": k0flops / t_k0 / 1e9 / FP64_PEAK_GFLOPS,
              "achieved_gbs": k0bytes / t_k0 / 1e9, "frac_hbm": k0bytes / t_k0 / 1e9 / hbm}
     st = hier.stats()
-    L = hier.n_levels
-    vcyc = (L - 1) * 9 + 2
-    body = 5 + vcyc                                            # SpMV+dot, update, V-cycle, dot, p, loop control
-    init = 7 + vcyc + (1 if args.form != "f64" else 0)        # begin, residual, norm, [cast], V-cycle, dot, p, loop
+    lc = hier.launches()
     n_iter = sum(its)
     # per step: ionic/RHS, the solve's set-up, one body per iteration (the body
-    # that detects convergence included), step end
-    launches = args.steps * (1 + init + 1) + n_iter * body + 5
+    # that detects convergence included), step end; per call: the gathers and
+    # scatters of u and w and the solver options
+    launches = args.steps * (1 + lc["per_setup"] + 1) + n_iter * lc["per_iteration"] + 3 + 2 * W.n_gates(wl.ionic)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
@@ -488,6 +504,8 @@ def run_ours(args, rank, world):
         "mdof_per_s": N * total_steps / t / 1e6,
         "config": bench_config(wl, args),
         "solver": {"form": args.form, "fine_operator": args.fine, "parallelism": f"replicas x{world}",
+                   "coarse_levels": "one persistent kernel" if lc["persistent"] else "separate kernels",
+                   "launches_per_vcycle": lc["per_vcycle"],
                    "levels": st["units"], "op_complexity": st["op_complexity"], "setup_s": setup_s,
                    "conditional_graph": os.environ.get("AGG_NO_COND_GRAPH") is None, "flexible_cg": flexible},
         "iterations": {"mean": float(np.mean(its)), "min": int(min(its)), "max": int(max(its)),
@@ -498,6 +516,7 @@ def run_ours(args, rank, world):
                 "same_steps_as_timed": args.e2e_steps == args.steps,
                 "same_final_state_as_timed": e2e_same},
         "roofline": roof, "fine_fp64_spmv": other,
+        **({"fine_fp64_matrix_free": mf64} if mf64 is not None else {}),
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "host_peak_rss_gb": resource.getrusage(resource.RUSAGE_SELF).ru_maxrss / 2**20,

@@ -83,6 +83,15 @@ typedef struct {
                                    the adjoint's conductivity gradient needs
                                    (volume form + 4 face blocks per neighbour;
                                    about 5x the stiffness memory)              */
+  /* Optional conductivity parameters (not in the paper; for gradients with
+   * respect to a coarse parameterisation): the assembly uses
+   * theta[theta_map[e]] * D_e in place of D_e. theta: host [n_theta], each
+   * finite and > 0; theta_map: host [n_elements] in [0, n_theta). NULL /
+   * 0 = none. Both are copied. agg_theta_gradient reduces per-element
+   * gradients to these parameters. */
+  const double* theta;
+  const int32_t* theta_map;
+  int64_t n_theta;
 } agg_mesh_desc;
 
 /* Assembles, on the host in float64, the SIPG stiffness A and the element
@@ -124,6 +133,15 @@ typedef struct {
                                     V-cycle, else AGG_EUNSUPPORTED. The outer
                                     CG always uses the assembled float64
                                     operator.                                */
+  int coarse_persistent;         /* 1: run levels >= 1 and the coarsest solve
+                                    of each V-cycle as one cooperative kernel
+                                    with grid-wide barriers (hierarchies of 3
+                                    or more levels, blocks of at most 32 DoFs;
+                                    otherwise ignored); 0 (default): one kernel
+                                    per level step. Same results bit for bit.
+                                    On GB300 a grid barrier costs ~3 us against
+                                    ~0.7 us between kernels of a CUDA graph,
+                                    so 0 is faster.                           */
 } agg_mg_opts;
 
 void agg_mg_opts_default(agg_mg_opts* opts);
@@ -171,7 +189,13 @@ agg_status agg_pcg_solve(agg_hier_t hier, const double* b_dev, double* x_dev,
 /* y = A_l x with the level's stored operator (float64 on level 0 always;
  * levels >= 1 in the V-cycle precision, converted from/to float64).
  * level = -1: the V-cycle's level-0 operator in the V-cycle precision (the
- * matrix-free one when fine_operator = 1). */
+ * matrix-free one when fine_operator = 1).
+ * level = -2: the level-0 operator evaluated matrix-free in float64 (the
+ * quadrature data of fine_operator = 1 kept in float64; built on the first
+ * such call; the mesh kinds of fine_operator = 1, in any V-cycle precision).
+ * It is a measured alternative to the assembled float64 operator of the
+ * outer CG, which keeps the assembled one (see agg_profile_kernel id 5).
+ * The mesh must stay alive while hierarchies built from it exist. */
 agg_status agg_operator_apply(agg_hier_t hier, int level, const double* x_dev, double* y_dev,
                               void* stream);
 /* z = B r: one V-cycle of the preconditioner (Section 6). */
@@ -323,6 +347,16 @@ agg_status agg_monodomain_adjoint_step(agg_sim_t sim, const double* u_n_dev, con
                                        const double* u_np1_dev, double* ubar_dev, double* wbar_dev,
                                        double* grad_logD_dev, void* stream);
 agg_status agg_monodomain_destroy(agg_sim_t sim);
+/* Chain rule from per-element log-conductivity gradients (the grad_logD_dev
+ * of agg_monodomain_adjoint_step, caller's element order) to the mesh's
+ * conductivity parameters: theta_grad_dev[k] += sum_{e: theta_map[e] = k}
+ * grad_logD_dev[e] / theta[k], since D_e = theta_k D0_e gives d log s_e =
+ * d theta_k / theta_k. On the device, one warp per parameter summing its
+ * elements in increasing element order (deterministic). Device arrays of
+ * n_elements and n_theta doubles, on the hierarchy's device. AGG_EINVAL if the
+ * hierarchy's mesh has no theta. Ordered on `stream`; does not synchronise. */
+agg_status agg_theta_gradient(agg_hier_t hier, const double* grad_logD_dev, double* theta_grad_dev,
+                              void* stream);
 
 /* ------------------------------------------------------------------ instrumentation
  * Kernel ids: 0 fine float64 SpMV y = A0 x (the outer CG's operator),
@@ -333,12 +367,26 @@ agg_status agg_monodomain_destroy(agg_sim_t sim);
  * can time it with events; agg_kernel_cost gives its algorithmic HBM bytes
  * (every matrix, block and vector entry read or written once) and flops per
  * launch. Kernels 1-3 need n_levels >= 2 (else AGG_EUNSUPPORTED).
+ * Id 5 is the level-0 operator evaluated matrix-free in float64 (the
+ * operator of agg_operator_apply level -2, built by the first call), the
+ * same product as id 0 from quadrature data instead of stored blocks; its
+ * flops are counted as id 0's (two per stored entry of the assembled
+ * operator), so the two ids compare as the same work.
  * agg_kernel_cost also takes id 4: one iteration of the solve body (float64
  * SpMV, CG update, one V-cycle over every level, z and p updates), the sum
  * of its launches' algorithmic bytes and flops, counting the float32 copy of
  * r and the flexible (r, z_old) read in the reduced-precision forms;
  * agg_profile_kernel rejects it (AGG_EINVAL). */
 agg_status agg_profile_kernel(agg_hier_t hier, int kernel, int reps, void* stream);
+/* Kernel launches of the solver's work, for launch accounting: per V-cycle,
+ * per PCG iteration (float64 SpMV, CG update, V-cycle, dot product, p update,
+ * loop control) and per solve set-up (the initial residual, its norm, the
+ * first V-cycle and p). *persistent is 1 when levels >= 1 and the coarsest
+ * solve run as one persistent kernel (hierarchies of 3 or more levels with
+ * blocks of at most 32 DoFs), 0 when they run as separate kernels per level
+ * and step. Host only; no device work. */
+agg_status agg_hier_launches(agg_hier_t hier, int* per_vcycle, int* per_iteration, int* per_setup,
+                             int* persistent);
 agg_status agg_kernel_cost(agg_hier_t hier, int kernel, double* bytes, double* flops);
 
 /* ------------------------------------------------------------------ host inspection

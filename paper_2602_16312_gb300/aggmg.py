@@ -32,14 +32,15 @@ class MeshDesc(C.Structure):
     _fields_ = [("dim", C.c_int), ("degree", C.c_int), ("n_vertices", C.c_int64), ("n_elements", C.c_int64),
                 ("vertices", C.POINTER(C.c_double)), ("elements", C.POINTER(C.c_int64)),
                 ("conductivity", C.POINTER(C.c_double)), ("penalty_mode", C.c_int),
-                ("penalty_coeff", C.c_double), ("quad_extra", C.c_int), ("adjoint_data", C.c_int)]
+                ("penalty_coeff", C.c_double), ("quad_extra", C.c_int), ("adjoint_data", C.c_int),
+                ("theta", C.POINTER(C.c_double)), ("theta_map", C.POINTER(C.c_int32)), ("n_theta", C.c_int64)]
 
 
 class MGOpts(C.Structure):
     _fields_ = [("n_levels", C.c_int), ("agg_maps", C.POINTER(C.POINTER(C.c_int32))),
                 ("smoother_degree", C.c_int), ("block_jacobi", C.c_int), ("lanczos_steps", C.c_int),
                 ("cheb_upper_safety", C.c_double), ("cheb_range", C.c_double), ("vcycle_precision", C.c_int),
-                ("fine_operator", C.c_int)]
+                ("fine_operator", C.c_int), ("coarse_persistent", C.c_int)]
 
 
 class PCGOpts(C.Structure):
@@ -104,6 +105,9 @@ _SIGS = {
     "agg_host_hierarchy_copy": [C.c_void_p, C.c_int, C.c_int, C.c_void_p],
     "agg_profile_kernel": [C.c_void_p, C.c_int, C.c_int, C.c_void_p],
     "agg_kernel_cost": [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+    "agg_theta_gradient": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "agg_hier_launches": [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                          C.POINTER(C.c_int)],
     "agg_status_string": [C.c_int],
     "agg_last_error": [],
 }
@@ -160,7 +164,7 @@ class Mesh:
     """agg_dg_mesh_create: SIPG stiffness and element mass blocks (host FP64)."""
 
     def __init__(self, vertices, elements, conductivity, degree, penalty_mode=1, penalty_coeff=10.0,
-                 quad_extra=1, adjoint_data=False):
+                 quad_extra=1, adjoint_data=False, theta=None, theta_map=None):
         self.vertices = np.ascontiguousarray(vertices, dtype=np.float64)
         self.elements = np.ascontiguousarray(elements, dtype=np.int64)
         self.conductivity = np.ascontiguousarray(conductivity, dtype=np.float64)
@@ -168,20 +172,27 @@ class Mesh:
         self.degree = degree
         self.B = (degree + 1) ** self.dim
         self.n_elements = self.elements.shape[0]
+        th, tm, nth = None, None, 0
+        if theta is not None:
+            self.theta = np.ascontiguousarray(theta, dtype=np.float64)
+            self.theta_map = np.ascontiguousarray(theta_map, dtype=np.int32)
+            th = self.theta.ctypes.data_as(C.POINTER(C.c_double))
+            tm = self.theta_map.ctypes.data_as(C.POINTER(C.c_int32))
+            nth = len(self.theta)
         d = MeshDesc(self.dim, degree, self.vertices.shape[0], self.n_elements,
                      self.vertices.ctypes.data_as(C.POINTER(C.c_double)),
                      self.elements.ctypes.data_as(C.POINTER(C.c_int64)),
                      self.conductivity.ctypes.data_as(C.POINTER(C.c_double)),
-                     penalty_mode, penalty_coeff, quad_extra, int(adjoint_data))
+                     penalty_mode, penalty_coeff, quad_extra, int(adjoint_data), th, tm, nth)
         h = C.c_void_p()
         _check(lib().agg_dg_mesh_create(C.byref(d), C.byref(h)))
         self.handle = h
 
     @classmethod
-    def from_workload(cls, wl, conductivity=None, adjoint_data=False):
+    def from_workload(cls, wl, conductivity=None, adjoint_data=False, theta=None, theta_map=None):
         D = wl.conductivity if conductivity is None else conductivity
         return cls(wl.mesh.vertices, wl.mesh.elements, D, wl.degree, wl.penalty_mode, wl.penalty_coeff,
-                   adjoint_data=adjoint_data)
+                   adjoint_data=adjoint_data, theta=theta, theta_map=theta_map)
 
     def locate(self, points):
         """(elem, weights) of agg_dg_mesh_locate for host points (n, dim)."""
@@ -247,7 +258,7 @@ FINE_OPERATORS = {"bsr": 0, "mf": 1}
 
 
 def _mg_opts(maps: Sequence[np.ndarray], precision="f64", block_jacobi=True, lanczos_steps=12,
-             safety=1.2, cheb_range=20.0, fine="bsr"):
+             safety=1.2, cheb_range=20.0, fine="bsr", coarse_persistent=False):
     o = MGOpts()
     lib().agg_mg_opts_default(C.byref(o))
     keep = [np.ascontiguousarray(m, dtype=np.int32) for m in maps]
@@ -262,6 +273,7 @@ def _mg_opts(maps: Sequence[np.ndarray], precision="f64", block_jacobi=True, lan
     o.cheb_range = cheb_range
     o.vcycle_precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.fine_operator = FINE_OPERATORS[fine] if isinstance(fine, str) else int(fine)
+    o.coarse_persistent = int(coarse_persistent)
     return o, (keep, arr)
 
 
@@ -351,6 +363,19 @@ class Hierarchy:
 
     def profile_kernel(self, kernel, reps, stream=None):
         _check(lib().agg_profile_kernel(self.handle, kernel, reps, C.c_void_p(_stream(stream))))
+
+    def theta_gradient(self, grad_logD, theta_grad, stream=None):
+        """agg_theta_gradient: theta_grad[k] += sum_{e in k} grad_logD[e] / theta[k]
+        (device tensors; the mesh's conductivity parameters)."""
+        _check(lib().agg_theta_gradient(self.handle, C.c_void_p(_dptr(grad_logD)), C.c_void_p(_dptr(theta_grad)),
+                                        C.c_void_p(_stream(stream))))
+
+    def launches(self):
+        """agg_hier_launches: kernel launches per V-cycle, per PCG iteration and
+        per solve set-up, and whether the coarse levels run persistently."""
+        v, i, s, p = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _check(lib().agg_hier_launches(self.handle, C.byref(v), C.byref(i), C.byref(s), C.byref(p)))
+        return dict(per_vcycle=v.value, per_iteration=i.value, per_setup=s.value, persistent=bool(p.value))
 
     def kernel_cost(self, kernel):
         b, f = C.c_double(), C.c_double()

@@ -2,10 +2,13 @@
 agg_monodomain_step whose backward runs agg_monodomain_adjoint_step (the
 discrete adjoint with the same MG-PCG) with checkpointing every K steps.
 
-Parameters: per-block conductivity scales theta, D_e = theta[theta_map[e]] D0_e.
-The library returns per-element log-conductivity gradients g_e; the chain
-rule gives dL/dtheta_k = sum_{e: theta_map[e] = k} g_e / theta_k.
-Only orchestration lives here; every step and reverse step runs in libaggmg.
+Parameters: per-block conductivity scales theta, D_e = theta[theta_map[e]] D0_e,
+passed to the library with the mesh (agg_mesh_desc.theta / theta_map). The
+reverse steps accumulate per-element log-conductivity gradients g_e on the
+device, and agg_theta_gradient applies the chain rule dL/dtheta_k =
+sum_{e: theta_map[e] = k} g_e / theta_k there. Only orchestration and
+argument marshalling live here; every step, reverse step and reduction runs
+in libaggmg.
 """
 from __future__ import annotations
 
@@ -32,8 +35,8 @@ class MonodomainProblem:
         self._built = None
 
     def build(self, theta: np.ndarray):
-        D = self.wl.conductivity * np.asarray(theta, dtype=np.float64)[self.theta_map][:, None, None]
-        mesh = aggmg.Mesh.from_workload(self.wl, conductivity=D, adjoint_data=True)
+        mesh = aggmg.Mesh.from_workload(self.wl, adjoint_data=True, theta=np.asarray(theta, dtype=np.float64),
+                                        theta_map=self.theta_map)
         hier = aggmg.Hierarchy(mesh, 1.0 / self.wl.dt, self.wl.maps, precision=self.precision)
         sim = aggmg.Monodomain(hier, self.wl.dt, self.wl.ionic, iapp_mask=self.mask, iapp_value=self.wl.iapp_value,
                                iapp_steps=self.wl.iapp_steps, rtol=self.rtol, flexible=self.flexible)
@@ -100,6 +103,7 @@ class MonodomainRun(torch.autograd.Function):
                 u_n, w_n = states[n - start]
                 u_np1 = states[n - start + 1][0]
                 sim.adjoint_step(u_n, w_n, u_np1, ubar, wbar, grad)
-        tmap = torch.tensor(problem.theta_map, device=dev)
-        gtheta = torch.zeros_like(theta, device=dev).index_add_(0, tmap, grad) / theta.to(dev)
+        _, hier, _ = ctx.objs
+        gtheta = torch.zeros(theta.numel(), dtype=torch.float64, device=dev)
+        hier.theta_gradient(grad, gtheta)
         return gtheta.to(theta.device), ubar, wbar, None, None, None

@@ -126,6 +126,19 @@ agg_status agg_dg_mesh_create(const agg_mesh_desc* d, agg_mesh_t* out) {
     m.X.assign(d->vertices, d->vertices + d->n_vertices * d->dim);
     m.cells.assign(d->elements, d->elements + d->n_elements * V);
     m.D.assign(d->conductivity, d->conductivity + d->n_elements * d->dim * d->dim);
+    if (d->theta || d->theta_map || d->n_theta) {
+      if (!d->theta || !d->theta_map || d->n_theta <= 0) return fail(AGG_EINVAL, "theta needs theta, theta_map and n_theta > 0");
+      m.theta.assign(d->theta, d->theta + d->n_theta);
+      m.theta_map.assign(d->theta_map, d->theta_map + d->n_elements);
+      for (double t : m.theta)
+        if (!(t > 0.0) || !std::isfinite(t)) return fail(AGG_EINVAL, "theta must be finite and > 0");
+      const int dd = d->dim * d->dim;
+      for (int64_t e = 0; e < d->n_elements; ++e) {
+        const int32_t k = m.theta_map[e];
+        if (k < 0 || k >= d->n_theta) return fail(AGG_EINVAL, "theta_map entry out of range");
+        for (int i = 0; i < dd; ++i) m.D[(size_t)e * dd + i] *= m.theta[k];
+      }
+    }
     m.penalty_mode = d->penalty_mode;
     m.penalty_coeff = d->penalty_coeff;
     m.quad_extra = d->quad_extra;
@@ -206,6 +219,7 @@ void agg_mg_opts_default(agg_mg_opts* o) {
   o->cheb_range = 20.0;
   o->vcycle_precision = AGG_F64;
   o->fine_operator = 0;
+  o->coarse_persistent = 0;
 }
 
 static agg_status check_mg_opts(const agg_mg_opts* o, double mass_coeff);
@@ -238,7 +252,7 @@ agg_status agg_mg_hierarchy_setup(agg_mesh_t mesh, double mass_coeff, const agg_
       h->lam_max.push_back(hh.lev[l].lam_max);
     }
     h->perm0 = hh.lev[0].perm;
-    s = eng->init(hh, m, o->vcycle_precision, o->fine_operator, (cudaStream_t)stream, err);
+    s = eng->init(hh, m, o->vcycle_precision, o->fine_operator, o->coarse_persistent, (cudaStream_t)stream, err);
     if (s) return fail((agg_status)s, err);
   } catch (const std::bad_alloc&) {
     return fail(AGG_ENOMEM, "host allocation failed");
@@ -250,6 +264,8 @@ agg_status agg_mg_hierarchy_setup(agg_mesh_t mesh, double mass_coeff, const agg_
 
 agg_status agg_mg_hierarchy_destroy(agg_hier_t h) {
   if (!h) return AGG_OK;
+  for (void* p : {(void*)h->d_tptr, (void*)h->d_tmem, (void*)h->d_theta})
+    if (p) cudaFree(p);
   delete h->eng;
   delete h;
   return AGG_OK;
@@ -285,6 +301,7 @@ static agg_status check_mg_opts(const agg_mg_opts* o, double mass_coeff) {
     return fail(AGG_EINVAL, "Chebyshev options");
   if (!(mass_coeff >= 0) || !std::isfinite(mass_coeff)) return fail(AGG_EINVAL, "mass_coeff");
   if (o->fine_operator != 0 && o->fine_operator != 1) return fail(AGG_EINVAL, "fine_operator");
+  if (o->coarse_persistent != 0 && o->coarse_persistent != 1) return fail(AGG_EINVAL, "coarse_persistent");
   return AGG_OK;
 }
 
@@ -489,8 +506,17 @@ agg_status agg_profile_kernel(agg_hier_t h, int kernel, int reps, void* stream) 
 agg_status agg_kernel_cost(agg_hier_t h, int kernel, double* bytes, double* flops) {
   if (!h || !bytes || !flops) return fail(AGG_EINVAL, "NULL argument");
   const int rc = h->eng->kernel_cost(kernel, *bytes, *flops);
-  if (rc == AGG_EUNSUPPORTED) return fail(AGG_EUNSUPPORTED, "kernels 1-3 need n_levels >= 2");
+  if (rc == AGG_EUNSUPPORTED)
+    return fail(AGG_EUNSUPPORTED, kernel == 5 ? "kernel 5 is built by its first agg_profile_kernel or "
+                                                "agg_operator_apply(level -2) call"
+                                              : "kernels 1-3 need n_levels >= 2");
   if (rc) return fail(AGG_EINVAL, "unknown kernel id");
+  return AGG_OK;
+}
+
+agg_status agg_hier_launches(agg_hier_t h, int* per_vcycle, int* per_iteration, int* per_setup, int* persistent) {
+  if (!h || !per_vcycle || !per_iteration || !per_setup || !persistent) return fail(AGG_EINVAL, "NULL argument");
+  h->eng->launch_counts(*per_vcycle, *per_iteration, *per_setup, *persistent);
   return AGG_OK;
 }
 

@@ -24,9 +24,14 @@ static __global__ void k_loop_ctl(CGState* st) {
   st->guard += 1;
 }
 
-// Reset of the per-solve fields; the options (rtol, atol, max_it, flexible,
-// cond, use_cond) are written by the host before the launch.
-static __global__ void k_cg_reset(CGState* st) {
+// Reset of the per-solve fields (and of the coarse-level kernel's grid
+// barrier, if any); the options (rtol, atol, max_it, flexible, cond,
+// use_cond) are written by the host before the launch.
+static __global__ void k_cg_reset(CGState* st, GridBar* bar) {
+  if (bar) {
+    bar->count = 0u;
+    bar->err = 0;
+  }
   st->guard = 0;
   st->iter = 0;
   st->done = 0;
@@ -35,8 +40,13 @@ static __global__ void k_cg_reset(CGState* st) {
   st->rz_old = 0.0;
 }
 
-// Start of a solve: reset and select the WHILE node that this launch ends.
-static __global__ void k_cg_begin(CGState* st, unsigned long long cond, int use_cond) {
+// Start of a solve: reset (with the coarse-level kernel's grid barrier, if
+// any) and select the WHILE node that this launch ends.
+static __global__ void k_cg_begin(CGState* st, unsigned long long cond, int use_cond, GridBar* bar) {
+  if (bar) {
+    bar->count = 0u;
+    bar->err = 0;
+  }
   st->iter = 0;
   st->done = 0;
   st->status = 0;

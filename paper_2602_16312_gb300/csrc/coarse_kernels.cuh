@@ -35,20 +35,42 @@ struct RowLane {
     unit = warp * UPW + sub;
     active = (sub < UPW) && (unit < n);
   }
+  // the same for an explicit warp index (persistent kernels loop over warps)
+  __device__ __forceinline__ RowLane(int64_t n, int64_t warp) {
+    lane = threadIdx.x & 31;
+    const int sub = lane / B;
+    r = lane - sub * B;
+    base = sub * B;
+    unit = warp * UPW + sub;
+    active = (sub < UPW) && (unit < n);
+  }
 };
 
-// (A x)_r of the lane's unit
+// (A x)_r of the lane's unit. The unit's lanes load up to B column ids of
+// its row at once (one coalesced load) and broadcast them by shuffles, so the
+// neighbour blocks' loads do not wait on a column-id load each; blocks are
+// still accumulated in row order. Called by every lane of the warp.
 template <typename T, int B>
 __device__ __forceinline__ T rl_row(const CsrBlocks<T>& A, const RowLane<B>& L, const T* __restrict__ x) {
   T s = T(0);
-  if (!L.active) return s;
-  const int j0 = A.rowptr[L.unit], j1 = A.rowptr[L.unit + 1];
-  for (int j = j0; j < j1; ++j) {
-    const int col = A.cols[j];
-    const T* blk = A.vals + (size_t)j * B * B + L.r;
-    const T* xb = x + (size_t)col * B;
+  int j0 = 0, len = 0;
+  if (L.active) {
+    j0 = A.rowptr[L.unit];
+    len = A.rowptr[L.unit + 1] - j0;
+  }
+  const int wmax = __reduce_max_sync(0xffffffffu, len);
+  for (int jb = 0; jb < wmax; jb += B) {
+    const int colv = (jb + L.r < len) ? A.cols[j0 + jb + L.r] : -1;
 #pragma unroll
-    for (int c = 0; c < B; ++c) s += blk[c * B] * xb[c];
+    for (int jj = 0; jj < B; ++jj) {
+      const int col = __shfl_sync(0xffffffffu, colv, (L.base + jj) & 31);
+      if (L.active && col >= 0) {
+        const T* blk = A.vals + (size_t)(j0 + jb + jj) * B * B + L.r;
+        const T* xb = x + (size_t)col * B;
+#pragma unroll
+        for (int c = 0; c < B; ++c) s += blk[c * B] * xb[c];
+      }
+    }
   }
   return s;
 }
@@ -76,7 +98,12 @@ static __global__ void __launch_bounds__(RL_NT) k_rl_cheb(CsrBlocks<T> A, const 
   const RowLane<B> L(A.n);
   const size_t o = (size_t)L.unit * B + L.r;
   T t = T(0);
-  if (L.active) t = (KIND == 0) ? rhs[o] : rhs[o] - rl_row<T, B>(A, L, x_old);
+  if constexpr (KIND == 0) {
+    if (L.active) t = rhs[o];
+  } else {
+    const T ax = rl_row<T, B>(A, L, x_old);       // every lane (warp shuffles)
+    if (L.active) t = rhs[o] - ax;
+  }
   const T s = rl_block<T, TD, B>(Dinv, L, t);
   if (!L.active) return;
   const T dn = (KIND == 2) ? c1 * d[o] + c2 * s : c2 * s;
@@ -93,7 +120,8 @@ static __global__ void __launch_bounds__(RL_NT) k_rl_resid_restrict(CsrBlocks<T>
   const RowLane<B> L(A.n);
   const size_t o = (size_t)L.unit * B + L.r;
   T t = T(0);
-  if (L.active) t = rhs[o] - rl_row<T, B>(A, L, x);
+  const T ax = rl_row<T, B>(A, L, x);             // every lane (warp shuffles)
+  if (L.active) t = rhs[o] - ax;
   // lane j (as column index) needs P[i][j] for all i: entries j*B + i, i.e. row j of P^T
   T s = T(0);
   const T* pj = P + (size_t)L.unit * B * B + (size_t)L.r * B;
@@ -124,6 +152,7 @@ static __global__ void __launch_bounds__(RL_NT) k_rl_prolong(const T* __restrict
 // y = A x (levels >= 1, for agg_operator_apply)
 template <typename T, int B>
 static __global__ void __launch_bounds__(RL_NT) k_rl_spmv(CsrBlocks<T> A, const T* __restrict__ x, T* __restrict__ y) {
+  // rl_row's shuffles need every lane of the warp: no early return
   const RowLane<B> L(A.n);
   const T s = rl_row<T, B>(A, L, x);
   if (L.active) y[(size_t)L.unit * B + L.r] = s;

@@ -22,6 +22,7 @@
 #include "face_op.cuh"
 #include "mf_kernels.cuh"
 #include "coarse_kernels.cuh"
+#include "coarse_persistent.cuh"
 
 namespace aggmg {
 
@@ -57,6 +58,17 @@ class Engine : public EngineBase {
   bool mf_ = false;
   MfOpT mfop_{};
   int64_t mf_bytes_ = 0;
+  // float64 matrix-free level-0 operator (a measured alternative to the
+  // face-structured float64 operator of the outer CG; built on first use)
+  static constexpr bool kMf64 = (B == 4 || B == 9 || B == 16 || B == 8 || B == 27);
+  using Mf64T = typename std::conditional<kMf64, typename MfOpForT<double, kMf64 ? B : 9>::type,
+                                          SellOp<double, B>>::type;
+  Mf64T mf64_{};
+  bool mf64_ready_ = false;
+  int64_t mf64_bytes_ = 0;
+  const Mesh* mesh_ = nullptr;
+  std::vector<int64_t> perm0_, inv0_;
+  double mass_coeff_ = 0.0;
   struct Lev {
     int64_t n = 0, nsl = 0, nvec = 0;
     int32_t* slice_ptr = nullptr;
@@ -79,6 +91,12 @@ class Engine : public EngineBase {
   std::vector<Lev> lev_;
   std::vector<int64_t> nnzb_;
   int num_sms_ = 152;
+  // persistent kernel for levels >= 1 and the coarsest solve (row-lane
+  // levels, at least one smoothed coarse level), when asked for
+  bool persist_ = false;
+  GridBar* bar_ = nullptr;
+  PCoarse<T, TD> pc_{};
+  int pgrid_ = 0;
 
   // Grid of a slice-looping unit kernel: one slice per warp. (Sizing the grid
   // to the resident warps and looping removes the partial last wave, but the
@@ -88,6 +106,46 @@ class Engine : public EngineBase {
     return std::max<int64_t>(1, cdiv(nsl * SL, NTB));
   }
   int nlev_ = 0, degree_ = 3;
+
+  // float64 quadrature data of the matrix-free operator (first use only)
+  int build_mf64(std::string& err) {
+    if (mf64_ready_) return AGG_OK;
+    if constexpr (!kMf64) {
+      err = "the float64 matrix-free operator needs quadrilaterals of p <= 3 or hexahedra of p <= 2";
+      return AGG_EUNSUPPORTED;
+    } else {
+      MatrixFreeData md;
+      int rc;
+      if ((rc = matrix_free_build(*mesh_, perm0_, inv0_, mass_coeff_, md, err))) return rc;
+      if (md.q != Mf64T::kDegree + 2) { err = "matrix-free operator needs quad_extra = 1"; return AGG_EUNSUPPORTED; }
+      double *cell, *face;
+      int32_t* nbr;
+      int8_t* code;
+      if ((rc = upload(&cell, md.cell.data(), md.cell.size(), err))) return rc;
+      if ((rc = upload(&face, md.face.data(), md.face.size(), err))) return rc;
+      if ((rc = upload(&nbr, md.nbr.data(), md.nbr.size(), err))) return rc;
+      if ((rc = upload(&code, md.code.data(), md.code.size(), err))) return rc;
+      mf64_.V = MfViewT<double>{cell, face, nbr, code, lev_[0].nsl};
+      Tables1D t1 = make_tables(mesh_->p, md.q);
+      std::memset(&mf64_.T, 0, sizeof(mf64_.T));
+      for (int a = 0; a <= mesh_->p; ++a) {
+        for (int kq = 0; kq < md.q; ++kq) {
+          double v[8], dv[8];
+          lagrange_eval(t1.gll.data(), mesh_->p + 1, t1.gx[kq], v, dv);
+          mf64_.T.L[a][kq] = v[a];
+          mf64_.T.D[a][kq] = dv[a];
+        }
+        for (int sd = 0; sd < 2; ++sd) {
+          double v[8], dv[8];
+          lagrange_eval(t1.gll.data(), mesh_->p + 1, (double)sd, v, dv);
+          mf64_.T.Dend[sd][a] = dv[a];
+        }
+      }
+      mf64_bytes_ = (int64_t)(md.cell.size() * 8 + md.face.size() * 8 + md.nbr.size() * 4 + md.code.size());
+      mf64_ready_ = true;
+      return AGG_OK;
+    }
+  }
   // level 0 in face-structured form: float64 for the outer CG, and the
   // V-cycle precision copy for the assembled smoother (the same data when
   // the V-cycle is float64)
@@ -292,10 +350,94 @@ class Engine : public EngineBase {
       if (l == 0 && mf_) return vc_level(l, mfop_, s);
     }
     if constexpr (kRL) {
+      if (l == 1 && persist_) return launch_persistent(s);
       if (l > 0) return vc_rowlane(l, s);
     }
     if (l == 0) return vc_level(l, fop_, s);
     return vc_level(l, SellOp<T, B>{v.A()}, s);
+  }
+
+  // Levels >= 1 and the coarsest solve in one cooperative launch; returns
+  // level 1's correction (the buffer the separate kernels would end in:
+  // 2 degree - 1 swaps of the ping-pong iterates).
+  T* launch_persistent(cudaStream_t s) {
+    if constexpr (kRL) {
+      cudaLaunchConfig_t cfg{};
+      cfg.gridDim = dim3((unsigned)pgrid_);
+      cfg.blockDim = dim3(PNT);
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeCooperative;
+      at[0].val.cooperative = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      cudaLaunchKernelEx(&cfg, k_coarse_persistent<T, TD, kRL ? B : 4>, pc_);
+    }
+    return ((2 * degree_ - 1) & 1) ? lev_[1].xb : lev_[1].xa;
+  }
+
+  // Fills the persistent kernel's level table; false if the hierarchy does
+  // not qualify (fewer than 3 levels, too many levels, no resident block).
+  bool setup_persistent(std::string& err) {
+    if constexpr (!kRL) {
+      return false;
+    } else {
+      if (nlev_ < 3 || nlev_ - 2 >= PMAXL || degree_ > PMAXDEG) return false;
+      int nb = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_coarse_persistent<T, TD, kRL ? B : 4>, PNT, 0) !=
+              cudaSuccess ||
+          nb < 1) {
+        cudaGetLastError();
+        return false;
+      }
+      pgrid_ = num_sms_ * nb;
+      if (!bar_ && dalloc(&bar_, 1, err)) return false;
+      pc_ = PCoarse<T, TD>{};
+      pc_.nl = nlev_ - 2;
+      pc_.degree = degree_;
+      for (int l = 1; l <= pc_.nl; ++l) {
+        const Lev& v = lev_[l];
+        PLevel<T, TD>& q = pc_.lev[l];
+        q.A = v.rl;
+        q.Dinv = v.rl_dinv;
+        q.P = v.rl_P;
+        q.parent = v.parent;
+        q.child_ptr = v.child_ptr;
+        q.rhs = v.rhs;
+        q.xa = v.xa;
+        q.xb = v.xb;
+        q.d = v.d;
+        q.S = v.S;
+        for (int k = 0; k < degree_; ++k) {
+          q.c1[k] = v.c1[k];
+          q.c2[k] = v.c2[k];
+        }
+        q.n = v.n;
+      }
+      const Lev& c = lev_[nlev_ - 1];
+      pc_.n_c_units = c.n;
+      pc_.child_ptr_c = c.child_ptr;
+      pc_.rhs_c = c.rhs;
+      pc_.x_c = c.xa;
+      pc_.Linv = Linv_;
+      pc_.U = U_;
+      pc_.yc = yc_;
+      pc_.nc = nc_;
+      pc_.bar = bar_;
+      pc_.st = st_;
+      // test hook: barriers that wait for arrivals that never come (their
+      // bounded spins then end the solve with AGG_ECUDA)
+      pc_.extra = getenv("AGG_PERSIST_TEST_EXTRA") ? (unsigned)std::max(0, atoi(getenv("AGG_PERSIST_TEST_EXTRA"))) : 0u;
+      return true;
+    }
+  }
+
+  // Kernel launches of one V-cycle from level l.
+  int vcycle_launches(int l) const {
+    if (l == nlev_ - 1) return 2;
+    if (l == 1 && persist_) return 1;
+    return 9 + vcycle_launches(l + 1);
   }
 
   // One coarse level (l >= 1) with the row-lane kernels.
@@ -371,7 +513,7 @@ class Engine : public EngineBase {
   }
 
   void launch_init(cudaStream_t s, unsigned long long cond, int use_cond) {
-    k_cg_begin<<<1, 1, 0, s>>>(st_, cond, use_cond);
+    k_cg_begin<<<1, 1, 0, s>>>(st_, cond, use_cond, persist_ ? bar_ : nullptr);
     k_spmv<double, B, 1, A0Op><<<bgrid(0, lev_[0].nsl), NTB, 0, s>>>(A0f_, x_, b_, r_, nullptr, nullptr);
     k_r0<<<RED_BLOCKS, RED_NT, 0, s>>>(r_, N0(), partials_, st_);
     launch_precond(s, true);
@@ -448,6 +590,47 @@ class Engine : public EngineBase {
     return AGG_OK;
   }
 
+  void end_dangling_capture() {
+    cudaGetLastError();
+    cudaStreamCaptureStatus cst;
+    if (cudaStreamIsCapturing(cs_, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+      cudaGraph_t dummy = nullptr;
+      cudaStreamEndCapture(cs_, &dummy);
+      if (dummy) cudaGraphDestroy(dummy);
+    }
+    cudaGetLastError();
+  }
+
+  void drop_solve_graphs() {
+    end_dangling_capture();
+    for (cudaGraphExec_t* e : {&solve_exec_, &init_exec_, &body_exec_})
+      if (*e) {
+        cudaGraphExecDestroy(*e);
+        *e = nullptr;
+      }
+  }
+
+  // The solve's graphs: set-up and iteration body (batch fallback) and the
+  // conditional WHILE graph. Without the persistent kernel a refused
+  // conditional node only selects the batch fallback; with it, any failure
+  // is returned so that the caller can retry with the separate kernels.
+  int build_solve_graphs(std::string& err) {
+    int rc;
+    if ((rc = capture([&](cudaStream_t c) { launch_init(c, 0, 0); }, &init_exec_, err))) return rc;
+    if ((rc = capture([&](cudaStream_t c) { launch_body(c); }, &body_exec_, err))) return rc;
+    std::string cerr;
+    use_cond_ = build_cond_graph([&](cudaStream_t c, unsigned long long hd, int u) { launch_init(c, hd, u); },
+                                 [&](cudaStream_t c) { k_noop<<<1, 1, 0, c>>>(); }, &solve_exec_, cerr) == AGG_OK;
+    if (!use_cond_) {
+      end_dangling_capture();
+      if (persist_) {
+        err = cerr;
+        return AGG_ECUDA;
+      }
+    }
+    return AGG_OK;
+  }
+
   // run a prepared solve on the internal buffers; batch fallback polls `done`
   int run_solve(cudaGraphExec_t cond_exec, cudaGraphExec_t pro, cudaGraphExec_t epi, cudaStream_t s,
                 std::string& err) {
@@ -483,9 +666,13 @@ class Engine : public EngineBase {
 
   bool uses_conditional_graph() const override { return use_cond_; }
 
-  int init(const HostHierarchy& h, const Mesh& m, int precision, int fine_operator, cudaStream_t s,
-           std::string& err) override {
+  int init(const HostHierarchy& h, const Mesh& m, int precision, int fine_operator, int coarse_persistent,
+           cudaStream_t s, std::string& err) override {
     (void)precision;
+    mesh_ = &m;
+    perm0_ = h.lev[0].perm;
+    inv0_ = h.lev[0].inv;
+    mass_coeff_ = h.mass_coeff;
     nlev_ = h.L;
     degree_ = 3;
     {
@@ -629,8 +816,11 @@ class Engine : public EngineBase {
         float *cell, *face;
         int32_t* nbr;
         int8_t* code;
-        if ((rc = upload(&cell, md.cell.data(), md.cell.size(), err))) return rc;
-        if ((rc = upload(&face, md.face.data(), md.face.size(), err))) return rc;
+        {
+          const std::vector<float> c32(md.cell.begin(), md.cell.end()), f32(md.face.begin(), md.face.end());
+          if ((rc = upload(&cell, c32.data(), c32.size(), err))) return rc;
+          if ((rc = upload(&face, f32.data(), f32.size(), err))) return rc;
+        }
         if ((rc = upload(&nbr, md.nbr.data(), md.nbr.size(), err))) return rc;
         if ((rc = upload(&code, md.code.data(), md.code.size(), err))) return rc;
         mfop_.V = MfView{cell, face, nbr, code, lev_[0].nsl};
@@ -675,22 +865,17 @@ class Engine : public EngineBase {
     if ((rc = dalloc(&partials_, nparts, err))) return rc;
     lev_[0].rhs = std::is_same<T, double>::value ? reinterpret_cast<T*>(r_) : reinterpret_cast<T*>(r32_);
     AGG_CK(cudaDeviceSynchronize());
-    // graphs: conditional WHILE solve, with the batch fallback prepared as well
-    if ((rc = capture([&](cudaStream_t c) { launch_init(c, 0, 0); }, &init_exec_, err))) return rc;
-    if ((rc = capture([&](cudaStream_t c) { launch_body(c); }, &body_exec_, err))) return rc;
-    std::string cerr;
-    use_cond_ = build_cond_graph([&](cudaStream_t c, unsigned long long hd, int u) { launch_init(c, hd, u); },
-                                 [&](cudaStream_t c) { k_noop<<<1, 1, 0, c>>>(); }, &solve_exec_, cerr) == AGG_OK;
-    if (!use_cond_) {
-      cudaGetLastError();
-      cudaStreamCaptureStatus cst;
-      if (cudaStreamIsCapturing(cs_, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
-        cudaGraph_t dummy = nullptr;
-        cudaStreamEndCapture(cs_, &dummy);
-        if (dummy) cudaGraphDestroy(dummy);
-      }
-      cudaGetLastError();
+    // graphs: conditional WHILE solve, with the batch fallback prepared as
+    // well; if the runtime refuses the cooperative launch of the coarse-level
+    // kernel inside a graph, the separate coarse kernels are captured instead
+    persist_ = coarse_persistent && setup_persistent(err);
+    for (;;) {
+      rc = build_solve_graphs(err);
+      if (rc == AGG_OK || !persist_) break;
+      drop_solve_graphs();
+      persist_ = false;
     }
+    if (rc) return rc;
     if (getenv("AGG_NO_COND_GRAPH")) use_cond_ = false;
     (void)s;
     return AGG_OK;
@@ -714,6 +899,10 @@ class Engine : public EngineBase {
     res.r0 = st_host_->r0;
     res.rn = std::sqrt(st_host_->rr);
     res.status = st_host_->status;
+    if (res.status == AGG_ECUDA) {
+      err = "a grid barrier of the coarse-level kernel timed out; the solve was stopped";
+      return AGG_ECUDA;
+    }
     return AGG_OK;
   }
 
@@ -729,6 +918,20 @@ class Engine : public EngineBase {
         k_op_apply<T, B, L0Op><<<bgrid(0, v.nsl), NTB, 0, s>>>(fop_, v.xa, v.xb);
       k_scatter_units<double, T><<<g, 256, 0, s>>>(v.xb, y_user, v.perm, v.n, B);
       AGG_CK(cudaGetLastError());
+      return AGG_OK;
+    }
+    if (l == -2) {
+      // the float64 matrix-free level-0 operator
+      int rc;
+      if ((rc = build_mf64(err))) return rc;
+      if constexpr (kMf64) {
+        Lev& v = lev_[0];
+        const int64_t g = cdiv(v.n * B, 256);
+        k_gather_units<double, double><<<g, 256, 0, s>>>(x_user, p_, v.perm, v.n, B);
+        k_op_apply<double, B, Mf64T><<<bgrid(0, v.nsl), NTB, 0, s>>>(mf64_, p_, q_);
+        k_scatter_units<double, double><<<g, 256, 0, s>>>(q_, y_user, v.perm, v.n, B);
+        AGG_CK(cudaGetLastError());
+      }
       return AGG_OK;
     }
     if (l < 0 || l >= nlev_) { err = "level out of range"; return AGG_EINVAL; }
@@ -751,7 +954,7 @@ class Engine : public EngineBase {
   int vcycle_apply(const double* r_user, double* z_user, cudaStream_t s, std::string& err) override {
     Lev& v = lev_[0];
     const int64_t g = cdiv(v.n * B, 256);
-    k_cg_reset<<<1, 1, 0, s>>>(st_);
+    k_cg_reset<<<1, 1, 0, s>>>(st_, persist_ ? bar_ : nullptr);
     k_gather_units<double, double><<<g, 256, 0, s>>>(r_user, r_, v.perm, v.n, B);
     if (!std::is_same<T, double>::value)
       k_cast<float, double><<<RED_BLOCKS, RED_NT, 0, s>>>(r_, r32_, N0(), st_);
@@ -884,7 +1087,17 @@ class Engine : public EngineBase {
   }
 
   int kernel_loop(int id, int reps, cudaStream_t s, std::string& err) override {
-    if (id >= 1 && nlev_ < 2) { err = "kernels 1-3 need a smoothed level 0 (n_levels >= 2)"; return AGG_EUNSUPPORTED; }
+    if (id == 5) {
+      int rc;
+      if ((rc = build_mf64(err))) return rc;
+      if constexpr (kMf64) {
+        for (int i = 0; i < reps; ++i)
+          k_spmv<double, B, 0, Mf64T><<<bgrid(0, lev_[0].nsl), NTB, 0, s>>>(mf64_, p_, nullptr, q_, nullptr, nullptr);
+        AGG_CK(cudaGetLastError());
+      }
+      return AGG_OK;
+    }
+    if (id >= 1 && id <= 3 && nlev_ < 2) { err = "kernels 1-3 need a smoothed level 0 (n_levels >= 2)"; return AGG_EUNSUPPORTED; }
     Lev& v = lev_[0];
     const int64_t n = v.nsl;
     for (int i = 0; i < reps; ++i) {
@@ -916,8 +1129,15 @@ class Engine : public EngineBase {
     return AGG_OK;
   }
 
+  void launch_counts(int& per_vcycle, int& per_iteration, int& per_setup, int& persistent) const override {
+    per_vcycle = vcycle_launches(0);
+    per_iteration = 5 + per_vcycle;   // SpMV + (p, q), CG update, V-cycle, (r, z), p update, loop control
+    per_setup = 6 + (std::is_same<T, double>::value ? 0 : 1) + per_vcycle;   // begin, residual, ||r0||, [cast], V-cycle, (r, z), p, loop control
+    persistent = persist_ ? 1 : 0;
+  }
+
   int kernel_cost(int id, double& bytes, double& flops) const override {
-    if (id >= 1 && nlev_ < 2) return AGG_EUNSUPPORTED;
+    if (id >= 1 && id <= 3 && nlev_ < 2) return AGG_EUNSUPPORTED;
     const double n0 = (double)lev_[0].n, N = n0 * B, bb = (double)B * B;
     const double sT = sizeof(T), sD = sizeof(TD);
     const double bd = (B <= 32) ? (double)SymPad<TD, B>::NP : bb;   // stored smoother entries
@@ -937,6 +1157,11 @@ class Engine : public EngineBase {
         break;
       case 3: bytes = n0 * bb * sT + 2 * N * sT + (double)lev_[1].n * B * sT + n0 * 4; flops = 2 * n0 * bb + N; break;
       case 4: iteration_cost(bytes, flops); break;
+      case 5:
+        if (!mf64_ready_) return AGG_EUNSUPPORTED;
+        bytes = (double)mf64_bytes_ + 2 * N * 8;
+        flops = 2 * fe;
+        break;
       default: return AGG_EINVAL;
     }
     return AGG_OK;

@@ -19,4 +19,9 @@ struct agg_hier {
   std::vector<double> lam_max;
   aggmg::EngineBase* eng = nullptr;
   bool sim_active = false;
+  // conductivity parameters on the device (uploaded by the first
+  // agg_theta_gradient): elements grouped by parameter (CSR) and theta
+  int32_t* d_tptr = nullptr;
+  int32_t* d_tmem = nullptr;
+  double* d_theta = nullptr;
 };

@@ -37,6 +37,15 @@ struct CGState {
   unsigned ticket[4];         // last-block tickets, one per reduction kind
 };
 
+// Grid-wide barrier state of the persistent coarse-level kernel: arrival
+// count, generation, error flag (set when a barrier times out).
+struct GridBar {
+  unsigned count;
+  unsigned gen;
+  int err;
+  int pad;
+};
+
 // ---------------------------------------------------------------- vector types
 template <typename T> struct Vec;
 template <> struct Vec<double> { using type = double2; static constexpr int W = 2; };

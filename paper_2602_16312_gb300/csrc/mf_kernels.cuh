@@ -23,40 +23,44 @@ template <> struct MfDegree<16> { static constexpr int value = 3; };
 // 1D tables: L[a][k] = l_a(x_k), D[a][k] = l_a'(x_k) at the Gauss points,
 // Dend[s][a] = l_a'(s) at the end points s = 0, 1 (l_a(s) is a Kronecker
 // delta on GLL nodes).
-struct MfTables {
-  float L[6][8];
-  float D[6][8];
-  float Dend[2][6];
+template <typename R>
+struct MfTablesT {
+  R L[6][8];
+  R D[6][8];
+  R Dend[2][6];
 };
+using MfTables = MfTablesT<float>;
 
-struct MfView {
-  const float* cell;     // [slice][qp*4 + comp][lane]
-  const float* face;     // [slice][f][q*5 + comp][lane]
+template <typename R>
+struct MfViewT {
+  const R* cell;         // [slice][qp*4 + comp][lane]
+  const R* face;         // [slice][f][q*5 + comp][lane]
   const int32_t* nbr;    // [slice][f][lane]
   const int8_t* code;    // [slice][f][lane]  neighbour face * 2 + reversed
   int64_t nslices;
 };
+using MfView = MfViewT<float>;
 
 // Neighbour trace values and reference gradients at the Q face points of its
 // local face (KN, SN), in its own tangential order.
-template <int P, int KN, int SN>
-__device__ __forceinline__ void mf_nbr_face(const MfTables& T, const float* xn, float* un, float* g0, float* g1) {
+template <typename R, int P, int KN, int SN>
+__device__ __forceinline__ void mf_nbr_face(const MfTablesT<R>& T, const R* xn, R* un, R* g0, R* g1) {
   constexpr int N = P + 1, Q = P + 2;
   const int fixed = SN * P;
-  float dn[N];
+  R dn[N];
 #pragma unroll
   for (int j = 0; j < N; ++j) {
-    float s = 0.f;
+    R s = R(0);
 #pragma unroll
     for (int i = 0; i < N; ++i) s += T.Dend[SN][i] * (KN == 0 ? xn[i + N * j] : xn[j + N * i]);
     dn[j] = s;
   }
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    float u = 0.f, gt = 0.f, gn = 0.f;
+    R u = R(0), gt = R(0), gn = R(0);
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      const float xf = (KN == 0) ? xn[fixed + N * j] : xn[j + N * fixed];
+      const R xf = (KN == 0) ? xn[fixed + N * j] : xn[j + N * fixed];
       u += T.L[j][q] * xf;
       gt += T.D[j][q] * xf;
       gn += T.L[j][q] * dn[j];
@@ -67,34 +71,38 @@ __device__ __forceinline__ void mf_nbr_face(const MfTables& T, const float* xn, 
   }
 }
 
-template <int B>
-struct MfOp {
+#ifndef AGG_MF2_MINB
+#define AGG_MF2_MINB 0
+#endif
+template <typename R, int B>
+struct MfOpV {
   static constexpr int kDegree = MfDegree<B>::value;
-  MfView V;
-  MfTables T;
+  static constexpr int kMinBlocks = AGG_MF2_MINB;
+  MfViewT<R> V;
+  MfTablesT<R> T;
   __device__ __forceinline__ int64_t nslices() const { return V.nslices; }
 
   // acc += ((c M + A) x)_e for the thread's element
-  __device__ __forceinline__ void apply(int64_t slice, int lane, const float* __restrict__ x, float* acc) const {
+  __device__ __forceinline__ void apply(int64_t slice, int lane, const R* __restrict__ x, R* acc) const {
     constexpr int P = MfDegree<B>::value, N = P + 1, Q = P + 2;
     const int64_t unit = slice * SL + lane;
-    float u[N * N];
+    R u[N * N];
 #pragma unroll
     for (int i = 0; i < N * N; ++i) u[i] = x[(size_t)unit * B + i];
 #ifndef AGG_MF_CELL_DIRECT
 #define AGG_MF_CELL_DIRECT 0
 #endif
-    const float* cd = V.cell + (size_t)slice * Q * Q * 4 * SL + lane;
+    const R* cd = V.cell + (size_t)slice * Q * Q * 4 * SL + lane;
     if constexpr (AGG_MF_CELL_DIRECT) {
       // ---- cell term point by point: more FP32 work, few live registers
 #pragma unroll 1
       for (int l = 0; l < Q; ++l) {
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
-          float uq = 0.f, g0 = 0.f, g1 = 0.f;
+          R uq = R(0), g0 = R(0), g1 = R(0);
 #pragma unroll
           for (int b = 0; b < N; ++b) {
-            float su = 0.f, sd = 0.f;
+            R su = R(0), sd = R(0);
 #pragma unroll
             for (int a = 0; a < N; ++a) {
               su += T.L[a][k] * u[a + N * b];
@@ -105,14 +113,14 @@ struct MfOp {
             g1 += T.D[b][l] * su;
           }
           const int iq = k + Q * l;
-          const float G00 = ld_once(cd + (iq * 4 + 0) * SL), G01 = ld_once(cd + (iq * 4 + 1) * SL);
-          const float G11 = ld_once(cd + (iq * 4 + 2) * SL), mm = ld_once(cd + (iq * 4 + 3) * SL);
-          const float w0 = G00 * g0 + G01 * g1;
-          const float w1 = G01 * g0 + G11 * g1;
-          const float wm = mm * uq;
+          const R G00 = ld_once(cd + (iq * 4 + 0) * SL), G01 = ld_once(cd + (iq * 4 + 1) * SL);
+          const R G11 = ld_once(cd + (iq * 4 + 2) * SL), mm = ld_once(cd + (iq * 4 + 3) * SL);
+          const R w0 = G00 * g0 + G01 * g1;
+          const R w1 = G01 * g0 + G11 * g1;
+          const R wm = mm * uq;
 #pragma unroll
           for (int b = 0; b < N; ++b) {
-            const float cb0 = T.L[b][l] * w0, cb1 = T.D[b][l] * w1 + T.L[b][l] * wm;
+            const R cb0 = T.L[b][l] * w0, cb1 = T.D[b][l] * w1 + T.L[b][l] * wm;
 #pragma unroll
             for (int a = 0; a < N; ++a) acc[a + N * b] += T.D[a][k] * cb0 + T.L[a][k] * cb1;
           }
@@ -120,12 +128,12 @@ struct MfOp {
       }
     } else {
     // ---- cell term by sum factorisation (index i = a + N b, qp = k + Q l)
-    float tu[N][Q], td[N][Q];
+    R tu[N][Q], td[N][Q];
 #pragma unroll
     for (int b = 0; b < N; ++b)
 #pragma unroll
       for (int k = 0; k < Q; ++k) {
-        float s0 = 0.f, s1 = 0.f;
+        R s0 = R(0), s1 = R(0);
 #pragma unroll
         for (int a = 0; a < N; ++a) {
           s0 += T.L[a][k] * u[a + N * b];
@@ -134,16 +142,47 @@ struct MfOp {
         tu[b][k] = s0;
         td[b][k] = s1;
       }
-    float p0[N][Q], p1[N][Q];
+#ifndef AGG_MF2_DIRECT_BACK
+#define AGG_MF2_DIRECT_BACK 0
+#endif
+    if constexpr (AGG_MF2_DIRECT_BACK) {
+      // back-projection of each Gauss point straight into acc (more FMAs,
+      // no p0/p1 partial sums held in registers)
+#pragma unroll
+      for (int l = 0; l < Q; ++l)
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+          R uq = R(0), g0 = R(0), g1 = R(0);
+#pragma unroll
+          for (int b = 0; b < N; ++b) {
+            uq += T.L[b][l] * tu[b][k];
+            g0 += T.L[b][l] * td[b][k];
+            g1 += T.D[b][l] * tu[b][k];
+          }
+          const int iq = k + Q * l;
+          const R G00 = ld_once(cd + (iq * 4 + 0) * SL), G01 = ld_once(cd + (iq * 4 + 1) * SL);
+          const R G11 = ld_once(cd + (iq * 4 + 2) * SL), mm = ld_once(cd + (iq * 4 + 3) * SL);
+          const R w0 = G00 * g0 + G01 * g1;
+          const R w1 = G01 * g0 + G11 * g1;
+          const R wm = mm * uq;
+#pragma unroll
+          for (int b = 0; b < N; ++b) {
+            const R cb0 = T.L[b][l] * w0, cb1 = T.D[b][l] * w1 + T.L[b][l] * wm;
+#pragma unroll
+            for (int a = 0; a < N; ++a) acc[a + N * b] += T.D[a][k] * cb0 + T.L[a][k] * cb1;
+          }
+        }
+    } else {
+    R p0[N][Q], p1[N][Q];
 #pragma unroll
     for (int b = 0; b < N; ++b)
 #pragma unroll
-      for (int k = 0; k < Q; ++k) { p0[b][k] = 0.f; p1[b][k] = 0.f; }
+      for (int k = 0; k < Q; ++k) { p0[b][k] = R(0); p1[b][k] = R(0); }
 #pragma unroll
     for (int l = 0; l < Q; ++l)
 #pragma unroll
       for (int k = 0; k < Q; ++k) {
-        float uq = 0.f, g0 = 0.f, g1 = 0.f;
+        R uq = R(0), g0 = R(0), g1 = R(0);
 #pragma unroll
         for (int b = 0; b < N; ++b) {
           uq += T.L[b][l] * tu[b][k];
@@ -151,11 +190,11 @@ struct MfOp {
           g1 += T.D[b][l] * tu[b][k];
         }
         const int iq = k + Q * l;
-        const float G00 = ld_once(cd + (iq * 4 + 0) * SL), G01 = ld_once(cd + (iq * 4 + 1) * SL);
-        const float G11 = ld_once(cd + (iq * 4 + 2) * SL), mm = ld_once(cd + (iq * 4 + 3) * SL);
-        const float w0 = G00 * g0 + G01 * g1;
-        const float w1 = G01 * g0 + G11 * g1;
-        const float wm = mm * uq;
+        const R G00 = ld_once(cd + (iq * 4 + 0) * SL), G01 = ld_once(cd + (iq * 4 + 1) * SL);
+        const R G11 = ld_once(cd + (iq * 4 + 2) * SL), mm = ld_once(cd + (iq * 4 + 3) * SL);
+        const R w0 = G00 * g0 + G01 * g1;
+        const R w1 = G01 * g0 + G11 * g1;
+        const R wm = mm * uq;
 #pragma unroll
         for (int b = 0; b < N; ++b) {
           p0[b][k] += T.L[b][l] * w0;
@@ -167,11 +206,12 @@ struct MfOp {
     for (int b = 0; b < N; ++b)
 #pragma unroll
       for (int a = 0; a < N; ++a) {
-        float s = 0.f;
+        R s = R(0);
 #pragma unroll
         for (int k = 0; k < Q; ++k) s += T.D[a][k] * p0[b][k] + T.L[a][k] * p1[b][k];
         acc[a + N * b] += s;
       }
+    }
     }
     // ---- face terms
 #pragma unroll
@@ -184,48 +224,48 @@ struct MfOp {
       const int KF = f / 2, SF = f % 2;
       const int fixed = SF * P;
       // own side: trace, tangential and normal derivatives at the face points
-      float dn[N];
+      R dn[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) {
-        float s = 0.f;
+        R s = R(0);
 #pragma unroll
         for (int i = 0; i < N; ++i) s += T.Dend[SF][i] * (KF == 0 ? u[i + N * j] : u[j + N * i]);
         dn[j] = s;
       }
-      float xn[N * N];
+      R xn[N * N];
 #pragma unroll
       for (int i = 0; i < N * N; ++i) xn[i] = x[(size_t)nb * B + i];
-      float un[Q], gn0[Q], gn1[Q];
+      R un[Q], gn0[Q], gn1[Q];
       switch (fn) {
-        case 0: mf_nbr_face<P, 0, 0>(T, xn, un, gn0, gn1); break;
-        case 1: mf_nbr_face<P, 0, 1>(T, xn, un, gn0, gn1); break;
-        case 2: mf_nbr_face<P, 1, 0>(T, xn, un, gn0, gn1); break;
-        default: mf_nbr_face<P, 1, 1>(T, xn, un, gn0, gn1); break;
+        case 0: mf_nbr_face<R, P, 0, 0>(T, xn, un, gn0, gn1); break;
+        case 1: mf_nbr_face<R, P, 0, 1>(T, xn, un, gn0, gn1); break;
+        case 2: mf_nbr_face<R, P, 1, 0>(T, xn, un, gn0, gn1); break;
+        default: mf_nbr_face<R, P, 1, 1>(T, xn, un, gn0, gn1); break;
       }
-      const float* fd = V.face + (size_t)((slice * 4 + f) * Q * 5) * SL + lane;
+      const R* fd = V.face + (size_t)((slice * 4 + f) * Q * 5) * SL + lane;
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
-        float up = 0.f, gt = 0.f, gn = 0.f;
+        R up = R(0), gt = R(0), gn = R(0);
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          const float xf = (KF == 0) ? u[fixed + N * j] : u[j + N * fixed];
+          const R xf = (KF == 0) ? u[fixed + N * j] : u[j + N * fixed];
           up += T.L[j][q] * xf;
           gt += T.D[j][q] * xf;
           gn += T.L[j][q] * dn[j];
         }
-        const float g0p = (KF == 0) ? gn : gt;
-        const float g1p = (KF == 0) ? gt : gn;
-        const float a0 = ld_once(fd + (q * 5 + 0) * SL), a1 = ld_once(fd + (q * 5 + 1) * SL);
-        const float b0 = ld_once(fd + (q * 5 + 2) * SL), b1 = ld_once(fd + (q * 5 + 3) * SL);
-        const float sq = ld_once(fd + (q * 5 + 4) * SL);
-        const float um = rev ? un[Q - 1 - q] : un[q];
-        const float h0 = rev ? gn0[Q - 1 - q] : gn0[q];
-        const float h1 = rev ? gn1[Q - 1 - q] : gn1[q];
-        const float flux = a0 * g0p + a1 * g1p + b0 * h0 + b1 * h1;
-        const float jump = up - um;
-        const float cf = -0.5f * flux + sq * jump;     // times phi_i on the face
-        const float cn = -0.5f * jump * (KF == 0 ? a0 : a1);   // times d phi_i / d xi_normal
-        const float ct = -0.5f * jump * (KF == 0 ? a1 : a0);   // times d phi_i / d xi_tangential
+        const R g0p = (KF == 0) ? gn : gt;
+        const R g1p = (KF == 0) ? gt : gn;
+        const R a0 = ld_once(fd + (q * 5 + 0) * SL), a1 = ld_once(fd + (q * 5 + 1) * SL);
+        const R b0 = ld_once(fd + (q * 5 + 2) * SL), b1 = ld_once(fd + (q * 5 + 3) * SL);
+        const R sq = ld_once(fd + (q * 5 + 4) * SL);
+        const R um = rev ? un[Q - 1 - q] : un[q];
+        const R h0 = rev ? gn0[Q - 1 - q] : gn0[q];
+        const R h1 = rev ? gn1[Q - 1 - q] : gn1[q];
+        const R flux = a0 * g0p + a1 * g1p + b0 * h0 + b1 * h1;
+        const R jump = up - um;
+        const R cf = R(-0.5) * flux + sq * jump;     // times phi_i on the face
+        const R cn = R(-0.5) * jump * (KF == 0 ? a0 : a1);   // times d phi_i / d xi_normal
+        const R ct = R(-0.5) * jump * (KF == 0 ? a1 : a0);   // times d phi_i / d xi_tangential
 #pragma unroll
         for (int j = 0; j < N; ++j) {
           // face DoFs: value and tangential derivative
@@ -258,21 +298,21 @@ template <> struct Mf3Degree<27> { static constexpr int value = 2; };
 #ifndef AGG_MF3_MINB
 #define AGG_MF3_MINB 0
 #endif
-template <int B>
-struct MfOp3 {
+template <typename R, int B>
+struct MfOp3V {
   static constexpr int kDegree = Mf3Degree<B>::value;
   static constexpr int kMinBlocks = AGG_MF3_MINB;
-  MfView V;
-  MfTables T;
+  MfViewT<R> V;
+  MfTablesT<R> T;
   __device__ __forceinline__ int64_t nslices() const { return V.nslices; }
 
-  __device__ __forceinline__ void apply(int64_t slice, int lane, const float* __restrict__ x, float* acc) const {
+  __device__ __forceinline__ void apply(int64_t slice, int lane, const R* __restrict__ x, R* acc) const {
     constexpr int P = kDegree, N = P + 1, Q = P + 2, NN = N * N, QQ = Q * Q;
     const int64_t unit = slice * SL + lane;
-    float u[B];
+    R u[B];
 #pragma unroll
     for (int i = 0; i < B; ++i) u[i] = x[(size_t)unit * B + i];
-    const float* cd = V.cell + (size_t)slice * QQ * Q * 7 * SL + lane;
+    const R* cd = V.cell + (size_t)slice * QQ * Q * 7 * SL + lane;
     // ---- cell term
 #ifndef AGG_MF3_PLANE_UNROLL
 #define AGG_MF3_PLANE_UNROLL 1
@@ -280,16 +320,16 @@ struct MfOp3 {
     constexpr int kPlaneUnroll = AGG_MF3_PLANE_UNROLL;
 #pragma unroll kPlaneUnroll
     for (int m = 0; m < Q; ++m) {
-      float Lm[N], Dm[N];
+      R Lm[N], Dm[N];
 #pragma unroll
       for (int c = 0; c < N; ++c) {
         Lm[c] = T.L[c][m];
         Dm[c] = T.D[c][m];
       }
-      float v[NN], w[NN];
+      R v[NN], w[NN];
 #pragma unroll
       for (int ab = 0; ab < NN; ++ab) {
-        float s0 = 0.f, s1 = 0.f;
+        R s0 = R(0), s1 = R(0);
 #pragma unroll
         for (int c = 0; c < N; ++c) {
           s0 += Lm[c] * u[ab + NN * c];
@@ -298,12 +338,12 @@ struct MfOp3 {
         v[ab] = s0;
         w[ab] = s1;
       }
-      float tu[N][Q], td[N][Q], tw[N][Q];
+      R tu[N][Q], td[N][Q], tw[N][Q];
 #pragma unroll
       for (int b = 0; b < N; ++b)
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
-          float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+          R s0 = R(0), s1 = R(0), s2 = R(0);
 #pragma unroll
           for (int a = 0; a < N; ++a) {
             s0 += T.L[a][k] * v[a + N * b];
@@ -314,16 +354,16 @@ struct MfOp3 {
           td[b][k] = s1;
           tw[b][k] = s2;
         }
-      float p0[N][Q], p1[N][Q], p2[N][Q];
+      R p0[N][Q], p1[N][Q], p2[N][Q];
 #pragma unroll
       for (int b = 0; b < N; ++b)
 #pragma unroll
-        for (int k = 0; k < Q; ++k) { p0[b][k] = 0.f; p1[b][k] = 0.f; p2[b][k] = 0.f; }
+        for (int k = 0; k < Q; ++k) { p0[b][k] = R(0); p1[b][k] = R(0); p2[b][k] = R(0); }
 #pragma unroll
       for (int l = 0; l < Q; ++l)
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
-          float uq = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+          R uq = R(0), g0 = R(0), g1 = R(0), g2 = R(0);
 #pragma unroll
           for (int b = 0; b < N; ++b) {
             uq += T.L[b][l] * tu[b][k];
@@ -331,14 +371,14 @@ struct MfOp3 {
             g1 += T.D[b][l] * tu[b][k];
             g2 += T.L[b][l] * tw[b][k];
           }
-          const float* gq = cd + (size_t)((k + Q * l + QQ * m) * 7) * SL;
-          const float G00 = ld_once(gq), G01 = ld_once(gq + SL), G02 = ld_once(gq + 2 * SL);
-          const float G11 = ld_once(gq + 3 * SL), G12 = ld_once(gq + 4 * SL), G22 = ld_once(gq + 5 * SL);
-          const float mm = ld_once(gq + 6 * SL);
-          const float w0 = G00 * g0 + G01 * g1 + G02 * g2;
-          const float w1 = G01 * g0 + G11 * g1 + G12 * g2;
-          const float w2 = G02 * g0 + G12 * g1 + G22 * g2;
-          const float wm = mm * uq;
+          const R* gq = cd + (size_t)((k + Q * l + QQ * m) * 7) * SL;
+          const R G00 = ld_once(gq), G01 = ld_once(gq + SL), G02 = ld_once(gq + 2 * SL);
+          const R G11 = ld_once(gq + 3 * SL), G12 = ld_once(gq + 4 * SL), G22 = ld_once(gq + 5 * SL);
+          const R mm = ld_once(gq + 6 * SL);
+          const R w0 = G00 * g0 + G01 * g1 + G02 * g2;
+          const R w1 = G01 * g0 + G11 * g1 + G12 * g2;
+          const R w2 = G02 * g0 + G12 * g1 + G22 * g2;
+          const R wm = mm * uq;
 #pragma unroll
           for (int b = 0; b < N; ++b) {
             p0[b][k] += T.L[b][l] * w0;
@@ -350,7 +390,7 @@ struct MfOp3 {
       for (int b = 0; b < N; ++b)
 #pragma unroll
         for (int a = 0; a < N; ++a) {
-          float pv = 0.f, pw = 0.f;
+          R pv = R(0), pw = R(0);
 #pragma unroll
           for (int k = 0; k < Q; ++k) {
             pv += T.D[a][k] * p0[b][k] + T.L[a][k] * p1[b][k];
@@ -365,31 +405,31 @@ struct MfOp3 {
     // thread's column of a shared array (no register array is indexed at run
     // time) and join acc at the end
     constexpr int NT = UnitThreads<B>::value;
-    __shared__ float sacc[B][NT];
+    __shared__ R sacc[B][NT];
     const int t = threadIdx.x;
 #pragma unroll
-    for (int i = 0; i < B; ++i) sacc[i][t] = 0.f;
-    const float* xe = x + (size_t)unit * B;
+    for (int i = 0; i < B; ++i) sacc[i][t] = R(0);
+    const R* xe = x + (size_t)unit * B;
 #pragma unroll 1
     for (int f = 0; f < 6; ++f) {
       const size_t fi = ((size_t)slice * 6 + f) * SL + lane;
       const int nb = V.nbr[fi];
       if (nb < 0) continue;
       const int fnb = V.code[fi];
-      float sU[N][Q], sT[N][Q], sN[N][Q], nU[N][Q], nT[N][Q], nN[N][Q];
+      R sU[N][Q], sT[N][Q], sN[N][Q], nU[N][Q], nT[N][Q], nN[N][Q];
       face_trace(xe, f, sU, sT, sN);
       face_trace(x + (size_t)nb * B, fnb, nU, nT, nN);
-      float rF[N][Q], rT[N][Q], rN[N][Q];
+      R rF[N][Q], rT[N][Q], rN[N][Q];
 #pragma unroll
       for (int j2 = 0; j2 < N; ++j2)
 #pragma unroll
-        for (int q1 = 0; q1 < Q; ++q1) { rF[j2][q1] = 0.f; rT[j2][q1] = 0.f; rN[j2][q1] = 0.f; }
-      const float* fd = V.face + (size_t)((slice * 6 + f) * QQ * 7) * SL + lane;
+        for (int q1 = 0; q1 < Q; ++q1) { rF[j2][q1] = R(0); rT[j2][q1] = R(0); rN[j2][q1] = R(0); }
+      const R* fd = V.face + (size_t)((slice * 6 + f) * QQ * 7) * SL + lane;
 #pragma unroll
       for (int q2 = 0; q2 < Q; ++q2)
 #pragma unroll
         for (int q1 = 0; q1 < Q; ++q1) {
-          float up = 0.f, gt0 = 0.f, gt1 = 0.f, gnn = 0.f, um = 0.f, ht0 = 0.f, ht1 = 0.f, hn = 0.f;
+          R up = R(0), gt0 = R(0), gt1 = R(0), gnn = R(0), um = R(0), ht0 = R(0), ht1 = R(0), hn = R(0);
 #pragma unroll
           for (int j2 = 0; j2 < N; ++j2) {
             up += T.L[j2][q2] * sU[j2][q1];
@@ -401,14 +441,14 @@ struct MfOp3 {
             ht1 += T.D[j2][q2] * nU[j2][q1];
             hn += T.L[j2][q2] * nN[j2][q1];
           }
-          const float* fq = fd + (size_t)((q1 + Q * q2) * 7) * SL;
-          const float aN = ld_once(fq), aT0 = ld_once(fq + SL), aT1 = ld_once(fq + 2 * SL);
-          const float bN = ld_once(fq + 3 * SL), bT0 = ld_once(fq + 4 * SL), bT1 = ld_once(fq + 5 * SL);
-          const float sq = ld_once(fq + 6 * SL);
-          const float flux = aN * gnn + aT0 * gt0 + aT1 * gt1 + bN * hn + bT0 * ht0 + bT1 * ht1;
-          const float jump = up - um;
-          const float cf = -0.5f * flux + sq * jump;
-          const float hj = -0.5f * jump;
+          const R* fq = fd + (size_t)((q1 + Q * q2) * 7) * SL;
+          const R aN = ld_once(fq), aT0 = ld_once(fq + SL), aT1 = ld_once(fq + 2 * SL);
+          const R bN = ld_once(fq + 3 * SL), bT0 = ld_once(fq + 4 * SL), bT1 = ld_once(fq + 5 * SL);
+          const R sq = ld_once(fq + 6 * SL);
+          const R flux = aN * gnn + aT0 * gt0 + aT1 * gt1 + bN * hn + bT0 * ht0 + bT1 * ht1;
+          const R jump = up - um;
+          const R cf = R(-0.5) * flux + sq * jump;
+          const R hj = R(-0.5) * jump;
 #pragma unroll
           for (int j2 = 0; j2 < N; ++j2) {
             rF[j2][q1] += T.L[j2][q2] * cf + T.D[j2][q2] * (hj * aT1);
@@ -425,7 +465,7 @@ struct MfOp3 {
       for (int j2 = 0; j2 < N; ++j2)
 #pragma unroll
         for (int j1 = 0; j1 < N; ++j1) {
-          float ff = 0.f, fnrm = 0.f;
+          R ff = R(0), fnrm = R(0);
 #pragma unroll
           for (int q1 = 0; q1 < Q; ++q1) {
             ff += T.L[j1][q1] * rF[j2][q1] + T.D[j1][q1] * rT[j2][q1];
@@ -434,9 +474,9 @@ struct MfOp3 {
           const int line = j1 * S0 + j2 * S1;
 #pragma unroll
           for (int i = 0; i < N; ++i) {
-            const float de = SF ? T.Dend[1][i] : T.Dend[0][i];
+            const R de = SF ? T.Dend[1][i] : T.Dend[0][i];
             const bool on_face = (SF ? P : 0) == i;
-            sacc[i * SK + line][t] += de * fnrm + (on_face ? ff : 0.f);
+            sacc[i * SK + line][t] += de * fnrm + (on_face ? ff : R(0));
           }
         }
     }
@@ -448,23 +488,23 @@ struct MfOp3 {
   // derivative (Nr) on local face f of the element whose DoFs start at xb,
   // interpolated to the Gauss points along the first tangential axis and
   // kept at the nodes along the second: [j2][q1].
-  __device__ __forceinline__ void face_trace(const float* __restrict__ xb, int f, float (&U)[kDegree + 1][kDegree + 2],
-                                             float (&Tn)[kDegree + 1][kDegree + 2],
-                                             float (&Nr)[kDegree + 1][kDegree + 2]) const {
+  __device__ __forceinline__ void face_trace(const R* __restrict__ xb, int f, R (&U)[kDegree + 1][kDegree + 2],
+                                             R (&Tn)[kDegree + 1][kDegree + 2],
+                                             R (&Nr)[kDegree + 1][kDegree + 2]) const {
     constexpr int P = kDegree, N = P + 1, Q = P + 2, NN = N * N;
     const int k = f >> 1, sd = f & 1;
     const int SK = (k == 0) ? 1 : (k == 1 ? N : NN);
     const int S0 = (k == 0) ? N : 1, S1 = (k == 2) ? N : NN;
-    const float* xf = xb + sd * P * SK;
+    const R* xf = xb + sd * P * SK;
 #pragma unroll
     for (int j2 = 0; j2 < N; ++j2) {
-      float tr[N], dn[N];
+      R tr[N], dn[N];
 #pragma unroll
       for (int j1 = 0; j1 < N; ++j1) {
-        float s = 0.f;
+        R s = R(0);
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-          const float de = sd ? T.Dend[1][i] : T.Dend[0][i];
+          const R de = sd ? T.Dend[1][i] : T.Dend[0][i];
           s += de * xb[i * SK + j1 * S0 + j2 * S1];
         }
         dn[j1] = s;
@@ -472,7 +512,7 @@ struct MfOp3 {
       }
 #pragma unroll
       for (int q1 = 0; q1 < Q; ++q1) {
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+        R a0 = R(0), a1 = R(0), a2 = R(0);
 #pragma unroll
         for (int j1 = 0; j1 < N; ++j1) {
           a0 += T.L[j1][q1] * tr[j1];
@@ -487,9 +527,13 @@ struct MfOp3 {
   }
 };
 
-template <int B> struct MfOpFor { using type = MfOp<B>; };
-template <> struct MfOpFor<8> { using type = MfOp3<8>; };
-template <> struct MfOpFor<27> { using type = MfOp3<27>; };
+template <int B> using MfOp = MfOpV<float, B>;
+template <int B> using MfOp3 = MfOp3V<float, B>;
+// matrix-free operator of value type R for B DoFs per element
+template <typename R, int B> struct MfOpForT { using type = MfOpV<R, B>; };
+template <typename R> struct MfOpForT<R, 8> { using type = MfOp3V<R, 8>; };
+template <typename R> struct MfOpForT<R, 27> { using type = MfOp3V<R, 27>; };
+template <int B> struct MfOpFor { using type = typename MfOpForT<float, B>::type; };
 
 // Sliced block-sparse operator in the same interface.
 template <typename T, int B>

@@ -34,7 +34,9 @@ struct Mesh {
   int64_t nv = 0, ne = 0;
   std::vector<double> X;         // [nv][dim]
   std::vector<int64_t> cells;    // [ne][2^dim]
-  std::vector<double> D;         // [ne][dim][dim]
+  std::vector<double> D;         // [ne][dim][dim] (scaled by theta when given)
+  std::vector<double> theta;     // [n_theta] conductivity parameters (optional)
+  std::vector<int32_t> theta_map;  // [ne] element -> parameter
   int penalty_mode = 1;
   double penalty_coeff = 10.0;
   int quad_extra = 1;
@@ -125,7 +127,7 @@ int hierarchy_build(const Mesh& m, double mass_coeff, const HierOptions& o, Host
 //   parametrise a shared face alike (same corner order).
 struct MatrixFreeData {
   int q = 0;
-  std::vector<float> cell, face;
+  std::vector<double> cell, face;   // float64; the float32 operator takes rounded copies
   std::vector<int32_t> nbr;
   std::vector<int8_t> code;
 };

@@ -661,8 +661,8 @@ int matrix_free_build(const Mesh& m, const std::vector<int64_t>& perm, const std
   const int64_t ne = m.ne;
   const int64_t nsl = (ne + 31) / 32;
   out.q = q;
-  out.cell.assign((size_t)nsl * 32 * Q * 4, 0.0f);
-  out.face.assign((size_t)nsl * 32 * nf * q * 5, 0.0f);
+  out.cell.assign((size_t)nsl * 32 * Q * 4, 0.0);
+  out.face.assign((size_t)nsl * 32 * nf * q * 5, 0.0);
   out.nbr.assign((size_t)nsl * 32 * nf, -1);
   out.code.assign((size_t)nsl * 32 * nf, 0);
   int fcorn[4][2];
@@ -694,7 +694,7 @@ int matrix_free_build(const Mesh& m, const std::vector<int64_t>& perm, const std
         }
       const double vals[4] = {G[0][0], G[0][1], G[1][1], c * w * det};
       for (int comp = 0; comp < 4; ++comp)
-        out.cell[((size_t)sl * Q * 4 + iq * 4 + comp) * 32 + lane] = (float)vals[comp];
+        out.cell[((size_t)sl * Q * 4 + iq * 4 + comp) * 32 + lane] = vals[comp];
     }
     // faces
     for (int f = 0; f < nf; ++f) {
@@ -753,7 +753,7 @@ int matrix_free_build(const Mesh& m, const std::vector<int64_t>& perm, const std
       for (int iq = 0; iq < q; ++iq) {
         const double vals[5] = {a0[iq], a1[iq], b0[iq], b1[iq], wdS[iq] * alpha * sg[iq]};
         for (int comp = 0; comp < 5; ++comp)
-          out.face[(((size_t)sl * nf + f) * q * 5 + iq * 5 + comp) * 32 + lane] = (float)vals[comp];
+          out.face[(((size_t)sl * nf + f) * q * 5 + iq * 5 + comp) * 32 + lane] = vals[comp];
       }
     }
   }
@@ -778,8 +778,8 @@ static int matrix_free_build_3d(const Mesh& m, const std::vector<int64_t>& perm,
   const int64_t ne = m.ne;
   const int64_t nsl = (ne + 31) / 32;
   out.q = q;
-  out.cell.assign((size_t)nsl * 32 * Q3 * 7, 0.0f);
-  out.face.assign((size_t)nsl * 32 * nf * Q2 * 7, 0.0f);
+  out.cell.assign((size_t)nsl * 32 * Q3 * 7, 0.0);
+  out.face.assign((size_t)nsl * 32 * nf * Q2 * 7, 0.0);
   out.nbr.assign((size_t)nsl * 32 * nf, -1);
   out.code.assign((size_t)nsl * 32 * nf, 0);
   int fcorn[6][4];
@@ -810,7 +810,7 @@ static int matrix_free_build_3d(const Mesh& m, const std::vector<int64_t>& perm,
         }
       const double vals[7] = {G[0][0], G[0][1], G[0][2], G[1][1], G[1][2], G[2][2], c * w * det};
       for (int comp = 0; comp < 7; ++comp)
-        out.cell[((size_t)sl * Q3 * 7 + iq * 7 + comp) * 32 + lane] = (float)vals[comp];
+        out.cell[((size_t)sl * Q3 * 7 + iq * 7 + comp) * 32 + lane] = vals[comp];
     }
     for (int f = 0; f < nf; ++f) {
       const int64_t rec = m.face_nbr[e * nf + f];
@@ -889,7 +889,7 @@ static int matrix_free_build_3d(const Mesh& m, const std::vector<int64_t>& perm,
         const double vals[7] = {av[iq * 3], av[iq * 3 + 1], av[iq * 3 + 2], bv[iq * 3], bv[iq * 3 + 1],
                                 bv[iq * 3 + 2], wdS[iq] * alpha * sg[iq]};
         for (int comp = 0; comp < 7; ++comp)
-          out.face[(((size_t)sl * nf + f) * Q2 * 7 + iq * 7 + comp) * 32 + lane] = (float)vals[comp];
+          out.face[(((size_t)sl * nf + f) * Q2 * 7 + iq * 7 + comp) * 32 + lane] = vals[comp];
       }
     }
   }

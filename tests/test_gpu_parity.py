@@ -7,7 +7,7 @@ from oracle import monodomain as omd
 from oracle import multigrid as omg
 from paper_2602_16312_gb300 import workloads as W
 
-from gpu_util import oracle_setup, rel, step_opts
+from gpu_util import oracle_setup, rel, step_opts, worst
 
 pytestmark = pytest.mark.gpu
 
@@ -158,3 +158,30 @@ def test_bdf2_trajectory_matches_oracle(name):
     # the mass coefficient must match the scheme
     with pytest.raises(aggmg.AggError):
         aggmg.Monodomain(hier, wl.dt, wl.ionic, scheme=0)
+
+
+def test_plain_fp64_square_all_fifty_steps_match_oracle_every_step():
+    """The 16x16 Q1 square as configured (plain float64, 2 levels of 4x4
+    agglomerates, rtol 1e-10, FitzHugh-Nagumo, stimulus for 5 steps, 50
+    steps from rest): after every step, the same PCG iteration count as the
+    oracle and u, w within 1e-10 of the oracle's largest entry."""
+    aggmg = _aggmg()
+    wl = W.square_2d_fhn(16, 1)
+    assert wl.n_steps == 50 and wl.rtol == 1e-10
+    disc, ho = oracle_setup(wl)
+    opts = step_opts(wl)
+    mask = wl.stim_mask_nodal()
+    hier = aggmg.Hierarchy(aggmg.Mesh.from_workload(wl), 1.0 / wl.dt, wl.maps, precision="f64")
+    sim = aggmg.Monodomain(hier, wl.dt, wl.ionic, iapp_mask=_dev(mask), iapp_value=wl.iapp_value,
+                           iapp_steps=wl.iapp_steps, rtol=wl.rtol)
+    u = torch.zeros(disc.n, dtype=torch.float64, device="cuda")
+    w = torch.zeros(disc.n, dtype=torch.float64, device="cuda")
+    uo, wo = np.zeros(disc.n), np.zeros(disc.n)
+    for n in range(wl.n_steps):
+        its = sim.step(u, w, 1)
+        uo, wo, res = omd.step(disc, ho, opts, uo, wo, mask, n)
+        assert its[0] == res.iterations, (n, its, res.iterations)
+        assert rel(u.cpu().numpy(), uo) <= 1e-10, (n, worst(u.cpu().numpy(), uo))
+        assert rel(w.cpu().numpy(), wo) <= 1e-10, (n, worst(w.cpu().numpy(), wo))
+    sim.close()
+    hier.close()

@@ -196,3 +196,21 @@ def test_locate_matches_oracle():
     np.testing.assert_allclose(w, wo, atol=1e-12)
     with pytest.raises(aggmg.AggError):
         m.locate(np.array([[1.5, 0.5]]))
+
+
+def test_theta_parameters_scale_the_conductivity():
+    """agg_mesh_desc.theta / theta_map: the assembly with theta[map[e]] D_e
+    equals, bit for bit, the assembly of the pre-scaled conductivities, and
+    bad parameters are rejected."""
+    wl = W.jittered_square_2d(n=6, degree=2, n_levels=2)
+    tmap, tshape = W.block_map(wl.mesh.grid_shape, (3, 3))
+    theta = np.exp(0.2 * np.random.default_rng(3).standard_normal(int(np.prod(tshape))))
+    a = aggmg.Mesh.from_workload(wl, theta=theta, theta_map=tmap).stiffness_bsr()
+    D = wl.conductivity * theta[tmap][:, None, None]
+    b = aggmg.Mesh.from_workload(wl, conductivity=D).stiffness_bsr()
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    for th, tm in ((-theta, tmap), (theta, tmap + len(theta)), (theta * np.nan, tmap)):
+        with pytest.raises(aggmg.AggError) as e:
+            aggmg.Mesh.from_workload(wl, theta=th, theta_map=tm)
+        assert e.value.status == aggmg.AGG_EINVAL
