@@ -81,13 +81,15 @@ WORKLOADS = {
 # is reported only while the kernel sources still hash to the captured value;
 # after any change to them, and for other configurations, traffic is null.
 NCU_TRAFFIC = {}
-KERNEL_SOURCES = ("kernels.cuh", "mf_kernels.cuh", "face_op.cuh", "coarse_kernels.cuh", "cg_kernels.cuh")
 
 
-def kernel_sources_hash():
+def kernel_sources_hash(fine):
+    """sha256 prefix of the sources that define the level-0 Chebyshev step of
+    the given level-0 operator (matrix-free or face-structured blocks)."""
     import hashlib
+    files = ("kernels.cuh", "mf_kernels.cuh") if fine == "mf" else ("kernels.cuh", "face_op.cuh")
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in files:
         with open(os.path.join(ROOT, "paper_2602_16312_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -451,7 +453,7 @@ def run_ours(args, rank, world):
         roof["frac_of_nominal"] = roof["achieved"] / HBM_NOMINAL_GBS
     roof["traffic"] = None
     cap = NCU_TRAFFIC.get((wl.name, args.form, args.fine, args.agglomeration, kid))
-    src_hash = kernel_sources_hash()
+    src_hash = kernel_sources_hash(args.fine)
     if cap is not None and cap[1] == src_hash:
         roof["traffic"] = cap[0]
         roof["traffic_source"] = (f"ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one launch) of "
@@ -504,7 +506,10 @@ def run_ours(args, rank, world):
         "mdof_per_s": N * total_steps / t / 1e6,
         "config": bench_config(wl, args),
         "solver": {"form": args.form, "fine_operator": args.fine, "parallelism": f"replicas x{world}",
-                   "coarse_levels": "one persistent kernel" if lc["persistent"] else "separate kernels",
+                   "coarse_levels": ("one persistent kernel" if lc["persistent"] else
+                                     f"separate kernels; levels >= {lc['cluster_level']} and the coarsest solve "
+                                     f"on one {lc['cluster_ctas']}-CTA cluster" if lc["cluster_level"] >= 0
+                                     else "separate kernels"),
                    "launches_per_vcycle": lc["per_vcycle"],
                    "levels": st["units"], "op_complexity": st["op_complexity"], "setup_s": setup_s,
                    "conditional_graph": os.environ.get("AGG_NO_COND_GRAPH") is None, "flexible_cg": flexible},

@@ -40,7 +40,7 @@ class MGOpts(C.Structure):
     _fields_ = [("n_levels", C.c_int), ("agg_maps", C.POINTER(C.POINTER(C.c_int32))),
                 ("smoother_degree", C.c_int), ("block_jacobi", C.c_int), ("lanczos_steps", C.c_int),
                 ("cheb_upper_safety", C.c_double), ("cheb_range", C.c_double), ("vcycle_precision", C.c_int),
-                ("fine_operator", C.c_int), ("coarse_persistent", C.c_int)]
+                ("fine_operator", C.c_int), ("coarse_persistent", C.c_int), ("coarse_cluster", C.c_int)]
 
 
 class PCGOpts(C.Structure):
@@ -107,7 +107,7 @@ _SIGS = {
     "agg_kernel_cost": [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "agg_theta_gradient": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "agg_hier_launches": [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
-                          C.POINTER(C.c_int)],
+                          C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "agg_status_string": [C.c_int],
     "agg_last_error": [],
 }
@@ -258,7 +258,7 @@ FINE_OPERATORS = {"bsr": 0, "mf": 1}
 
 
 def _mg_opts(maps: Sequence[np.ndarray], precision="f64", block_jacobi=True, lanczos_steps=12,
-             safety=1.2, cheb_range=20.0, fine="bsr", coarse_persistent=False):
+             safety=1.2, cheb_range=20.0, fine="bsr", coarse_persistent=False, coarse_cluster=False):
     o = MGOpts()
     lib().agg_mg_opts_default(C.byref(o))
     keep = [np.ascontiguousarray(m, dtype=np.int32) for m in maps]
@@ -274,6 +274,7 @@ def _mg_opts(maps: Sequence[np.ndarray], precision="f64", block_jacobi=True, lan
     o.vcycle_precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.fine_operator = FINE_OPERATORS[fine] if isinstance(fine, str) else int(fine)
     o.coarse_persistent = int(coarse_persistent)
+    o.coarse_cluster = int(coarse_cluster)
     return o, (keep, arr)
 
 
@@ -373,9 +374,11 @@ class Hierarchy:
     def launches(self):
         """agg_hier_launches: kernel launches per V-cycle, per PCG iteration and
         per solve set-up, and whether the coarse levels run persistently."""
-        v, i, s, p = C.c_int(), C.c_int(), C.c_int(), C.c_int()
-        _check(lib().agg_hier_launches(self.handle, C.byref(v), C.byref(i), C.byref(s), C.byref(p)))
-        return dict(per_vcycle=v.value, per_iteration=i.value, per_setup=s.value, persistent=bool(p.value))
+        v, i, s, p, cl, cc = (C.c_int() for _ in range(6))
+        _check(lib().agg_hier_launches(self.handle, C.byref(v), C.byref(i), C.byref(s), C.byref(p), C.byref(cl),
+                                       C.byref(cc)))
+        return dict(per_vcycle=v.value, per_iteration=i.value, per_setup=s.value, persistent=bool(p.value),
+                    cluster_level=cl.value, cluster_ctas=cc.value)
 
     def kernel_cost(self, kernel):
         b, f = C.c_double(), C.c_double()

@@ -220,6 +220,7 @@ void agg_mg_opts_default(agg_mg_opts* o) {
   o->vcycle_precision = AGG_F64;
   o->fine_operator = 0;
   o->coarse_persistent = 0;
+  o->coarse_cluster = 0;
 }
 
 static agg_status check_mg_opts(const agg_mg_opts* o, double mass_coeff);
@@ -252,7 +253,8 @@ agg_status agg_mg_hierarchy_setup(agg_mesh_t mesh, double mass_coeff, const agg_
       h->lam_max.push_back(hh.lev[l].lam_max);
     }
     h->perm0 = hh.lev[0].perm;
-    s = eng->init(hh, m, o->vcycle_precision, o->fine_operator, o->coarse_persistent, (cudaStream_t)stream, err);
+    s = eng->init(hh, m, o->vcycle_precision, o->fine_operator, o->coarse_persistent, o->coarse_cluster,
+                  (cudaStream_t)stream, err);
     if (s) return fail((agg_status)s, err);
   } catch (const std::bad_alloc&) {
     return fail(AGG_ENOMEM, "host allocation failed");
@@ -302,6 +304,7 @@ static agg_status check_mg_opts(const agg_mg_opts* o, double mass_coeff) {
   if (!(mass_coeff >= 0) || !std::isfinite(mass_coeff)) return fail(AGG_EINVAL, "mass_coeff");
   if (o->fine_operator != 0 && o->fine_operator != 1) return fail(AGG_EINVAL, "fine_operator");
   if (o->coarse_persistent != 0 && o->coarse_persistent != 1) return fail(AGG_EINVAL, "coarse_persistent");
+  if (o->coarse_cluster != 0 && o->coarse_cluster != 1) return fail(AGG_EINVAL, "coarse_cluster");
   return AGG_OK;
 }
 
@@ -514,9 +517,13 @@ agg_status agg_kernel_cost(agg_hier_t h, int kernel, double* bytes, double* flop
   return AGG_OK;
 }
 
-agg_status agg_hier_launches(agg_hier_t h, int* per_vcycle, int* per_iteration, int* per_setup, int* persistent) {
+agg_status agg_hier_launches(agg_hier_t h, int* per_vcycle, int* per_iteration, int* per_setup, int* persistent,
+                             int* cluster_level, int* cluster_ctas) {
   if (!h || !per_vcycle || !per_iteration || !per_setup || !persistent) return fail(AGG_EINVAL, "NULL argument");
-  h->eng->launch_counts(*per_vcycle, *per_iteration, *per_setup, *persistent);
+  int cl = -1, cc = 0;
+  h->eng->launch_counts(*per_vcycle, *per_iteration, *per_setup, *persistent, cl, cc);
+  if (cluster_level) *cluster_level = cl;
+  if (cluster_ctas) *cluster_ctas = cc;
   return AGG_OK;
 }
 

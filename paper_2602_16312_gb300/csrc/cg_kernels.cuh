@@ -102,9 +102,33 @@ static __global__ void __launch_bounds__(RED_NT) k_cg_update(double* __restrict_
   const double alpha = st->alpha;
   const bool flex = st->flexible != 0;
   double s = 0.0, sz = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * RED_NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_NT) {
+  // pairs of entries per 16-byte access (n is even: whole 32-unit slices),
+  // a scalar tail otherwise
+  const int64_t n2 = n >> 1;
+  for (int64_t i = (int64_t)blockIdx.x * RED_NT + threadIdx.x; i < n2; i += (int64_t)gridDim.x * RED_NT) {
+    double2 xv = reinterpret_cast<double2*>(x)[i];
+    double2 rv = reinterpret_cast<double2*>(r)[i];
+    const double2 pv = reinterpret_cast<const double2*>(p)[i];
+    const double2 qv = reinterpret_cast<const double2*>(q)[i];
+    xv.x += alpha * pv.x;
+    xv.y += alpha * pv.y;
+    rv.x = rv.x - alpha * qv.x;
+    rv.y = rv.y - alpha * qv.y;
+    reinterpret_cast<double2*>(x)[i] = xv;
+    reinterpret_cast<double2*>(r)[i] = rv;
+    s += rv.x * rv.x;
+    s += rv.y * rv.y;
+    if (flex) {
+      const double2 zv = reinterpret_cast<const double2*>(zold)[i];
+      sz += rv.x * zv.x;
+      sz += rv.y * zv.y;
+    }
+    if (r32) reinterpret_cast<float2*>(r32)[i] = make_float2((float)rv.x, (float)rv.y);
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t i = n - 1;
     x[i] += alpha * p[i];
-    double ri = r[i] - alpha * q[i];
+    const double ri = r[i] - alpha * q[i];
     r[i] = ri;
     s += ri * ri;
     if (flex) sz += ri * zold[i];
@@ -144,10 +168,20 @@ static __global__ void __launch_bounds__(RED_NT) k_zdot(const TZ* __restrict__ z
                                                  CGState* st) {
   if (st->done) return;
   double s = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * RED_NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_NT) {
-    const double zn = (double)zin[i];
-    z64[i] = zn;
-    s += r[i] * zn;
+  using Z2 = typename std::conditional<std::is_same<TZ, float>::value, float2, double2>::type;
+  const int64_t n2 = n >> 1;
+  for (int64_t i = (int64_t)blockIdx.x * RED_NT + threadIdx.x; i < n2; i += (int64_t)gridDim.x * RED_NT) {
+    const Z2 zv = reinterpret_cast<const Z2*>(zin)[i];
+    const double2 rv = reinterpret_cast<const double2*>(r)[i];
+    const double2 zn = make_double2((double)zv.x, (double)zv.y);
+    reinterpret_cast<double2*>(z64)[i] = zn;
+    s += rv.x * zn.x;
+    s += rv.y * zn.y;
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    const double zn = (double)zin[n - 1];
+    z64[n - 1] = zn;
+    s += r[n - 1] * zn;
   }
   if (partial_and_last<RED_NT>(s, partials, &st->ticket[TK_Z])) {
     const double rz = sum_partials<RED_NT>(partials, gridDim.x);
@@ -166,8 +200,19 @@ static __global__ void __launch_bounds__(RED_NT) k_pupd(const double* __restrict
                                                  const CGState* st) {
   if (st->done) return;
   const double beta = st->beta;
-  for (int64_t i = (int64_t)blockIdx.x * RED_NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_NT)
-    p[i] = INIT ? z[i] : z[i] + beta * p[i];
+  const int64_t n2 = n >> 1;
+  for (int64_t i = (int64_t)blockIdx.x * RED_NT + threadIdx.x; i < n2; i += (int64_t)gridDim.x * RED_NT) {
+    const double2 zv = reinterpret_cast<const double2*>(z)[i];
+    if (INIT) {
+      reinterpret_cast<double2*>(p)[i] = zv;
+    } else {
+      double2 pv = reinterpret_cast<double2*>(p)[i];
+      pv.x = zv.x + beta * pv.x;
+      pv.y = zv.y + beta * pv.y;
+      reinterpret_cast<double2*>(p)[i] = pv;
+    }
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) p[n - 1] = INIT ? z[n - 1] : z[n - 1] + beta * p[n - 1];
 }
 
 template <typename TO, typename TI>

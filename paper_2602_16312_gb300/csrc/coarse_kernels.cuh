@@ -46,30 +46,56 @@ struct RowLane {
   }
 };
 
-// (A x)_r of the lane's unit. The unit's lanes load up to B column ids of
-// its row at once (one coalesced load) and broadcast them by shuffles, so the
-// neighbour blocks' loads do not wait on a column-id load each; blocks are
-// still accumulated in row order. Called by every lane of the warp.
+// (A x)_r of the lane's unit. The row's blocks are taken RL_GROUP at a time:
+// the column ids, block entries and neighbour values of a group are loaded
+// unconditionally (indices past the row's end clamped to its first block)
+// before any of them is used, so their latencies overlap instead of forming a
+// chain of dependent loads per block; the sum then adds the valid blocks in
+// row order, as one block at a time would. (Loading ids together and
+// broadcasting them by warp shuffles, under a per-block branch, measured
+// slower on GB300: 16.6 against 11.8 us per level-1 Chebyshev step.)
+#ifndef AGG_RL_GROUP
+#define AGG_RL_GROUP 1
+#endif
 template <typename T, int B>
 __device__ __forceinline__ T rl_row(const CsrBlocks<T>& A, const RowLane<B>& L, const T* __restrict__ x) {
+  constexpr int G = AGG_RL_GROUP;
   T s = T(0);
-  int j0 = 0, len = 0;
-  if (L.active) {
-    j0 = A.rowptr[L.unit];
-    len = A.rowptr[L.unit + 1] - j0;
-  }
-  const int wmax = __reduce_max_sync(0xffffffffu, len);
-  for (int jb = 0; jb < wmax; jb += B) {
-    const int colv = (jb + L.r < len) ? A.cols[j0 + jb + L.r] : -1;
+  if (!L.active) return s;
+  const int j0 = A.rowptr[L.unit], j1 = A.rowptr[L.unit + 1];
+  if constexpr (G == 1) {
+    for (int j = j0; j < j1; ++j) {
+      const int col = A.cols[j];
+      const T* blk = A.vals + (size_t)j * B * B + L.r;
+      const T* xb = x + (size_t)col * B;
 #pragma unroll
-    for (int jj = 0; jj < B; ++jj) {
-      const int col = __shfl_sync(0xffffffffu, colv, (L.base + jj) & 31);
-      if (L.active && col >= 0) {
-        const T* blk = A.vals + (size_t)(j0 + jb + jj) * B * B + L.r;
-        const T* xb = x + (size_t)col * B;
+      for (int c = 0; c < B; ++c) s += blk[c * B] * xb[c];
+    }
+  } else {
+    for (int jb = j0; jb < j1; jb += G) {
+      int jj[G], col[G];
 #pragma unroll
-        for (int c = 0; c < B; ++c) s += blk[c * B] * xb[c];
+      for (int t = 0; t < G; ++t) {
+        jj[t] = (jb + t < j1) ? jb + t : j0;
+        col[t] = A.cols[jj[t]];
       }
+      T bv[G][B], xv[G][B];
+#pragma unroll
+      for (int t = 0; t < G; ++t) {
+        const T* blk = A.vals + (size_t)jj[t] * B * B + L.r;
+        const T* xb = x + (size_t)col[t] * B;
+#pragma unroll
+        for (int c = 0; c < B; ++c) {
+          bv[t][c] = blk[c * B];
+          xv[t][c] = xb[c];
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < G; ++t)
+        if (jb + t < j1) {
+#pragma unroll
+          for (int c = 0; c < B; ++c) s += bv[t][c] * xv[t][c];
+        }
     }
   }
   return s;
@@ -101,7 +127,7 @@ static __global__ void __launch_bounds__(RL_NT) k_rl_cheb(CsrBlocks<T> A, const 
   if constexpr (KIND == 0) {
     if (L.active) t = rhs[o];
   } else {
-    const T ax = rl_row<T, B>(A, L, x_old);       // every lane (warp shuffles)
+    const T ax = rl_row<T, B>(A, L, x_old);
     if (L.active) t = rhs[o] - ax;
   }
   const T s = rl_block<T, TD, B>(Dinv, L, t);
@@ -120,7 +146,7 @@ static __global__ void __launch_bounds__(RL_NT) k_rl_resid_restrict(CsrBlocks<T>
   const RowLane<B> L(A.n);
   const size_t o = (size_t)L.unit * B + L.r;
   T t = T(0);
-  const T ax = rl_row<T, B>(A, L, x);             // every lane (warp shuffles)
+  const T ax = rl_row<T, B>(A, L, x);
   if (L.active) t = rhs[o] - ax;
   // lane j (as column index) needs P[i][j] for all i: entries j*B + i, i.e. row j of P^T
   T s = T(0);
@@ -152,7 +178,6 @@ static __global__ void __launch_bounds__(RL_NT) k_rl_prolong(const T* __restrict
 // y = A x (levels >= 1, for agg_operator_apply)
 template <typename T, int B>
 static __global__ void __launch_bounds__(RL_NT) k_rl_spmv(CsrBlocks<T> A, const T* __restrict__ x, T* __restrict__ y) {
-  // rl_row's shuffles need every lane of the warp: no early return
   const RowLane<B> L(A.n);
   const T s = rl_row<T, B>(A, L, x);
   if (L.active) y[(size_t)L.unit * B + L.r] = s;

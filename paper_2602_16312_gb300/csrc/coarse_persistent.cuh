@@ -1,28 +1,37 @@
-// Persistent kernel for the coarse part of the V-cycle (Section 6): every
-// level l >= 1 with its Chebyshev block-Jacobi steps, residual restriction,
-// segmented sums, prolongation, and the coarsest level's Cholesky solve, in
-// one launch. Coarse levels are small (16K..64 units on the 2D benchmark
-// workload), so as separate kernels they cost about 20 launches of a few
-// microseconds each per V-cycle, mostly launch latency and idle tails; here
-// the phases are separated by grid-wide barriers instead.
+// Coarse part of the V-cycle (Section 6) in one launch: the levels from a
+// first level on, with their Chebyshev block-Jacobi steps, residual
+// restriction, segmented sums, prolongation, and the coarsest level's
+// Cholesky solve, the steps separated by barriers instead of kernel
+// boundaries. Two forms:
+//   k_coarse_persistent: levels >= 1 on the whole GPU, cooperative launch,
+//     software grid barrier (agg_mg_opts.coarse_persistent);
+//   k_coarse_cluster: the smallest levels (each at most 16 x 1024 rows) on
+//     one thread-block cluster of 16 (else 8) CTAs, separated by the
+//     cluster's hardware barrier (agg_mg_opts.coarse_cluster).
 //
-// Each phase does, per (unit, row) or per coarsest row, exactly the
+// Each step does, per (unit, row) or per coarsest row, exactly the
 // arithmetic of the corresponding separate kernel (k_rl_cheb,
 // k_rl_resid_restrict, k_segsum, k_rl_prolong, k_coarse_lower/upper) in the
-// same order, so both paths give bitwise the same correction.
+// same order, so all paths give bitwise the same correction.
 //
-// Measured on GB300 (512^2 Q2 workload, float32 V-cycle): a grid barrier
-// costs 2.7-3.9 us (152-608 blocks) while consecutive kernels of a CUDA
-// graph start 0.7 us apart, so this kernel (653 us per V-cycle) loses to the
-// separate kernels (597 us); it is an option (agg_mg_opts.coarse_persistent),
-// not the default.
+// Measured on GB300 (float32 V-cycle), both are options and not defaults:
+//   - a grid barrier costs 2.7-3.9 us (152-608 blocks), while consecutive
+//     kernels of a CUDA graph start 0.7 us apart; V-cycle of the 512^2 Q2
+//     workload 646-653 us persistent against 593-597 us separate;
+//   - the cluster kernel: 593.8 against 595.6 us (512^2 Q2, levels 2-3),
+//     3,067 against 3,037 us (64^3 Q2 cube), 3,184 against 3,110 us (shell).
+//   The coarse steps are bound by each thread's chain of dependent loads
+//   (neighbour column id, then its block values), which fusing launches does
+//   not shorten.
 //
-// The launch is cooperative (all blocks resident). Every barrier spins a
-// bounded number of times: if the limit is reached the kernel records an
+// The cooperative launch keeps all blocks resident. Every grid barrier spins
+// a bounded number of times: if the limit is reached the kernel records an
 // error, marks the solve done with status AGG_ECUDA and every block leaves
 // at its next barrier, so a failure ends the solve instead of hanging it.
+// The cluster barrier is the hardware's; every CTA of the cluster reaches
+// each one (the early exit on a finished solve is taken by all of them).
 //
-// Vectors written by one phase and read by a later one are read with
+// Vectors written by one step and read by a later one are read with
 // __ldcg (L2, coherent); operator, block and map data with __ldg.
 #pragma once
 #include "coarse_kernels.cuh"
@@ -49,8 +58,9 @@ struct PLevel {
 
 template <typename T, typename TD>
 struct PCoarse {
-  PLevel<T, TD> lev[PMAXL];       // lev[l] for l = 1 .. nl (the smoothed coarse levels)
-  int nl;                         // number of smoothed coarse levels (L - 2)
+  PLevel<T, TD> lev[PMAXL];       // lev[l] for l = first .. nl (the smoothed coarse levels run here)
+  int first;                      // first level run here (1 for the grid-wide kernel)
+  int nl;                         // last smoothed level (L - 2)
   int degree;
   // coarsest level (index nl + 1)
   int64_t n_c_units;
@@ -109,24 +119,14 @@ __device__ __forceinline__ bool grid_sync(GridBar* b, unsigned extra) {
 template <typename T, int B>
 __device__ __forceinline__ T p_row(const CsrBlocks<T>& A, const RowLane<B>& L, const T* x) {
   T s = T(0);
-  int j0 = 0, len = 0;
-  if (L.active) {
-    j0 = __ldg(A.rowptr + L.unit);
-    len = __ldg(A.rowptr + L.unit + 1) - j0;
-  }
-  const int wmax = __reduce_max_sync(0xffffffffu, len);
-  for (int jb = 0; jb < wmax; jb += B) {
-    const int colv = (jb + L.r < len) ? __ldg(A.cols + j0 + jb + L.r) : -1;
+  if (!L.active) return s;
+  const int j0 = __ldg(A.rowptr + L.unit), j1 = __ldg(A.rowptr + L.unit + 1);
+  for (int j = j0; j < j1; ++j) {
+    const int col = __ldg(A.cols + j);
+    const T* blk = A.vals + (size_t)j * B * B + L.r;
+    const T* xb = x + (size_t)col * B;
 #pragma unroll
-    for (int jj = 0; jj < B; ++jj) {
-      const int col = __shfl_sync(0xffffffffu, colv, (L.base + jj) & 31);
-      if (L.active && col >= 0) {
-        const T* blk = A.vals + (size_t)(j0 + jb + jj) * B * B + L.r;
-        const T* xb = x + (size_t)col * B;
-#pragma unroll
-        for (int c = 0; c < B; ++c) s += __ldg(blk + c * B) * __ldcg(xb + c);
-      }
-    }
+    for (int c = 0; c < B; ++c) s += __ldg(blk + c * B) * __ldcg(xb + c);
   }
   return s;
 }
@@ -151,7 +151,7 @@ __device__ __forceinline__ void p_cheb(const PLevel<T, TD>& v, const T* x_old, T
   if constexpr (KIND == 0) {
     if (L.active) t = __ldcg(v.rhs + o);
   } else {
-    const T ax = p_row<T, B>(v.A, L, x_old);      // every lane (warp shuffles)
+    const T ax = p_row<T, B>(v.A, L, x_old);
     if (L.active) t = __ldcg(v.rhs + o) - ax;
   }
   const T s = p_block<T, TD, B>(v.Dinv, L, t);
@@ -166,7 +166,7 @@ __device__ __forceinline__ void p_resid_restrict(const PLevel<T, TD>& v, const T
   const RowLane<B> L(v.A.n, warp);
   const size_t o = (size_t)L.unit * B + L.r;
   T t = T(0);
-  const T ax = p_row<T, B>(v.A, L, x);            // every lane (warp shuffles)
+  const T ax = p_row<T, B>(v.A, L, x);
   if (L.active) t = __ldcg(v.rhs + o) - ax;
   T s = T(0);
   const T* pj = v.P + (size_t)L.unit * B * B + (size_t)L.r * B;
@@ -184,6 +184,7 @@ __device__ __forceinline__ void p_segsum(const int64_t* child_ptr, const T* S, T
   const int64_t K = id / B;
   const int j = (int)(id % B);
   T s = T(0);
+#pragma unroll 4
   for (int64_t u = __ldg(child_ptr + K); u < __ldg(child_ptr + K + 1); ++u) s += __ldcg(S + (size_t)u * B + j);
   rc[id] = s;
 }
@@ -206,6 +207,7 @@ __device__ __forceinline__ void p_coarse_lower(const double* Linv, const T* r, d
   if (row >= n) return;
   const double* Lr = Linv + (size_t)row * n;
   double s = 0.0;
+#pragma unroll 8
   for (int64_t k = lane; k <= row; k += 32) s += __ldg(Lr + k) * (double)__ldcg(r + k);
   s = warp_sum(s);
   if (lane == 0) y[row] = s;
@@ -217,6 +219,7 @@ __device__ __forceinline__ void p_coarse_upper(const double* U, const double* y,
   if (row >= n) return;
   const double* Ur = U + (size_t)row * n;
   double s = 0.0;
+#pragma unroll 8
   for (int64_t k = row + lane; k < n; k += 32) s += __ldg(Ur + k) * __ldcg(y + k);
   s = warp_sum(s);
   if (lane == 0) z[row] = (T)s;
@@ -228,21 +231,37 @@ __device__ __forceinline__ int64_t rl_warps(int64_t n) {
   return (n + RowLane<B>::UPW - 1) / RowLane<B>::UPW;
 }
 
-template <typename T, typename TD, int B>
-static __global__ void __launch_bounds__(PNT, 5) k_coarse_persistent(PCoarse<T, TD> P) {
-  if (P.st->done) return;
+// Phase barriers: the software grid barrier of the cooperative kernel, or the
+// hardware barrier of a thread-block cluster (barrier.cluster arrive/wait with
+// release/acquire semantics at cluster scope).
+struct GridSync {
+  GridBar* bar;
+  unsigned extra;
+  __device__ __forceinline__ bool operator()() const { return grid_sync(bar, extra); }
+};
+struct ClusterSync {
+  __device__ __forceinline__ bool operator()() const {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    return true;
+  }
+};
+
+// The coarse part of one V-cycle from level P.first down to the coarsest and
+// back, on all NTH * gridDim.x threads; level P.first's right-hand side is in
+// place. Returns after the last post-smoothing step of level P.first.
+template <typename T, typename TD, int B, int NTH, typename Sync>
+__device__ __forceinline__ void coarse_cycle(const PCoarse<T, TD>& P, Sync sync) {
   const int lane = threadIdx.x & 31;
-  const int64_t gwarp = ((int64_t)blockIdx.x * PNT + threadIdx.x) >> 5;
-  const int64_t nwarp = ((int64_t)gridDim.x * PNT) >> 5;
-  const int64_t gthr = (int64_t)blockIdx.x * PNT + threadIdx.x;
-  const int64_t nthr = (int64_t)gridDim.x * PNT;
+  const int64_t gwarp = ((int64_t)blockIdx.x * NTH + threadIdx.x) >> 5;
+  const int64_t nwarp = ((int64_t)gridDim.x * NTH) >> 5;
+  const int64_t gthr = (int64_t)blockIdx.x * NTH + threadIdx.x;
+  const int64_t nthr = (int64_t)gridDim.x * NTH;
   T* xo[PMAXL + 1];
   T* xn[PMAXL + 1];
-  bool ok = true;
-#define AGG_PHASE_END                   \
-  if (!(ok = grid_sync(P.bar, P.extra))) goto fail;
+#define AGG_PHASE_END \
+  if (!sync()) goto fail;
   // ---- down: pre-smoothing, residual, restriction
-  for (int l = 1; l <= P.nl; ++l) {
+  for (int l = P.first; l <= P.nl; ++l) {
     const PLevel<T, TD>& v = P.lev[l];
     xo[l] = v.xa;
     xn[l] = v.xb;
@@ -268,7 +287,7 @@ static __global__ void __launch_bounds__(PNT, 5) k_coarse_persistent(PCoarse<T, 
   AGG_PHASE_END
   for (int64_t row = gwarp; row < P.nc; row += nwarp) p_coarse_upper<T>(P.U, P.yc, P.x_c, P.nc, row, lane);
   // ---- up: prolongation and post-smoothing
-  for (int l = P.nl; l >= 1; --l) {
+  for (int l = P.nl; l >= P.first; --l) {
     AGG_PHASE_END
     const PLevel<T, TD>& v = P.lev[l];
     const T* ec = (l == P.nl) ? P.x_c : xo[l + 1];
@@ -290,6 +309,23 @@ fail:
     P.st->status = AGG_ECUDA;
     P.st->done = 1;
   }
+}
+
+// Levels >= 1 on the whole GPU (cooperative launch, software grid barrier).
+template <typename T, typename TD, int B>
+static __global__ void __launch_bounds__(PNT, 5) k_coarse_persistent(PCoarse<T, TD> P) {
+  if (P.st->done) return;
+  coarse_cycle<T, TD, B, PNT>(P, GridSync{P.bar, P.extra});
+}
+
+// The smallest levels (from P.first on, each at most CNT x cluster-size
+// rows) in one thread-block cluster of up to 16 CTAs: the grid is the
+// cluster, phases are separated by the cluster's hardware barrier.
+constexpr int CNT = 1024;
+template <typename T, typename TD, int B>
+static __global__ void __launch_bounds__(CNT, 1) k_coarse_cluster(PCoarse<T, TD> P) {
+  if (P.st->done) return;
+  coarse_cycle<T, TD, B, CNT>(P, ClusterSync{});
 }
 
 }  // namespace aggmg

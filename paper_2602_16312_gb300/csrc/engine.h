@@ -37,7 +37,7 @@ class EngineBase {
   virtual ~EngineBase() {}
   // upload the host hierarchy (and element mass blocks) and capture graphs
   virtual int init(const HostHierarchy& h, const Mesh& m, int precision, int fine_operator, int coarse_persistent,
-                   cudaStream_t s,
+                   int coarse_cluster, cudaStream_t s,
                    std::string& err) = 0;
   virtual int pcg_solve(const double* b_user, double* x_user, const SolveOpts& o, SolveResult& res,
                         cudaStream_t s, std::string& err) = 0;
@@ -59,7 +59,8 @@ class EngineBase {
   virtual int kernel_cost(int id, double& bytes, double& flops) const = 0;
   // kernel launches of one V-cycle, one solve-body iteration and one solve
   // set-up; whether the coarse levels run in the persistent kernel
-  virtual void launch_counts(int& per_vcycle, int& per_iteration, int& per_setup, int& persistent) const = 0;
+  virtual void launch_counts(int& per_vcycle, int& per_iteration, int& per_setup, int& persistent,
+                             int& cluster_level, int& cluster_ctas) const = 0;
   // y = A_l x with the permuted copies of x and y in caller-provided device
   // scratch (s_in, s_out: at least level_scratch_entries(l) doubles each)
   virtual int64_t level_scratch_entries(int level) const = 0;

@@ -97,6 +97,11 @@ class Engine : public EngineBase {
   GridBar* bar_ = nullptr;
   PCoarse<T, TD> pc_{};
   int pgrid_ = 0;
+  // thread-block cluster kernel for the smallest levels (from lc_ on, each of
+  // at most csize_ x CNT rows) and the coarsest solve
+  bool cluster_ = false;
+  int lc_ = 0, csize_ = 0;
+  PCoarse<T, TD> pcc_{};
 
   // Grid of a slice-looping unit kernel: one slice per warp. (Sizing the grid
   // to the resident warps and looping removes the partial last wave, but the
@@ -340,6 +345,9 @@ class Engine : public EngineBase {
   // holding the correction.
   T* vc(int l, cudaStream_t s) {
     Lev& v = lev_[l];
+    if constexpr (kRL) {
+      if (cluster_ && l == lc_) return launch_cluster(s);
+    }
     if (l == nlev_ - 1) {
       const int64_t g = cdiv(nc_ * 32, 256);
       k_coarse_lower<T><<<g, 256, 0, s>>>(Linv_, v.rhs, yc_, nc_, st_);
@@ -393,12 +401,24 @@ class Engine : public EngineBase {
       }
       pgrid_ = num_sms_ * nb;
       if (!bar_ && dalloc(&bar_, 1, err)) return false;
-      pc_ = PCoarse<T, TD>{};
-      pc_.nl = nlev_ - 2;
-      pc_.degree = degree_;
-      for (int l = 1; l <= pc_.nl; ++l) {
+      fill_table(pc_, 1);
+      // test hook: barriers that wait for arrivals that never come (their
+      // bounded spins then end the solve with AGG_ECUDA)
+      pc_.extra = getenv("AGG_PERSIST_TEST_EXTRA") ? (unsigned)std::max(0, atoi(getenv("AGG_PERSIST_TEST_EXTRA"))) : 0u;
+      return true;
+    }
+  }
+
+  // Level table of the coarse-cycle kernels from level `first` on.
+  void fill_table(PCoarse<T, TD>& pc, int first) {
+    {
+      pc = PCoarse<T, TD>{};
+      pc.first = first;
+      pc.nl = nlev_ - 2;
+      pc.degree = degree_;
+      for (int l = first; l <= pc.nl; ++l) {
         const Lev& v = lev_[l];
-        PLevel<T, TD>& q = pc_.lev[l];
+        PLevel<T, TD>& q = pc.lev[l];
         q.A = v.rl;
         q.Dinv = v.rl_dinv;
         q.P = v.rl_P;
@@ -416,25 +436,87 @@ class Engine : public EngineBase {
         q.n = v.n;
       }
       const Lev& c = lev_[nlev_ - 1];
-      pc_.n_c_units = c.n;
-      pc_.child_ptr_c = c.child_ptr;
-      pc_.rhs_c = c.rhs;
-      pc_.x_c = c.xa;
-      pc_.Linv = Linv_;
-      pc_.U = U_;
-      pc_.yc = yc_;
-      pc_.nc = nc_;
-      pc_.bar = bar_;
-      pc_.st = st_;
-      // test hook: barriers that wait for arrivals that never come (their
-      // bounded spins then end the solve with AGG_ECUDA)
-      pc_.extra = getenv("AGG_PERSIST_TEST_EXTRA") ? (unsigned)std::max(0, atoi(getenv("AGG_PERSIST_TEST_EXTRA"))) : 0u;
-      return true;
+      pc.n_c_units = c.n;
+      pc.child_ptr_c = c.child_ptr;
+      pc.rhs_c = c.rhs;
+      pc.x_c = c.xa;
+      pc.Linv = Linv_;
+      pc.U = U_;
+      pc.yc = yc_;
+      pc.nc = nc_;
+      pc.bar = bar_;
+      pc.st = st_;
+      pc.extra = 0u;
     }
+  }
+
+  // The cluster kernel: first level lc_ (the first level whose rows fit one
+  // pass of the cluster), cluster of 16 CTAs where the device schedules one,
+  // else 8. False when no level qualifies below level 1 or no cluster fits.
+  bool setup_cluster() {
+    if constexpr (!kRL) {
+      return false;
+    } else {
+      if (nlev_ < 2 || nlev_ - 2 >= PMAXL || degree_ > PMAXDEG) return false;
+      auto kern = k_coarse_cluster<T, TD, kRL ? B : 4>;
+      for (int cs : {16, 8}) {
+        if (cs > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+          cudaGetLastError();
+          continue;
+        }
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)cs);
+        cfg.blockDim = dim3(CNT);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)cs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclus = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclus, kern, &cfg) != cudaSuccess || nclus < 1) {
+          cudaGetLastError();
+          continue;
+        }
+        const int64_t cap = (int64_t)cs * CNT;
+        int lc = nlev_ - 1;
+        for (int l = nlev_ - 2; l >= 1 && lev_[l].n * B <= cap; --l) lc = l;
+        if (lc < 1) return false;
+        lc_ = lc;
+        csize_ = cs;
+        fill_table(pcc_, lc_);
+        return true;
+      }
+      return false;
+    }
+  }
+
+  // Levels lc_ .. L-1 in one cluster launch; returns level lc_'s correction
+  // (the coarsest's solution when lc_ is the coarsest level).
+  T* launch_cluster(cudaStream_t s) {
+    if constexpr (kRL) {
+      cudaLaunchConfig_t cfg{};
+      cfg.gridDim = dim3((unsigned)csize_);
+      cfg.blockDim = dim3(CNT);
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = (unsigned)csize_;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      cudaLaunchKernelEx(&cfg, k_coarse_cluster<T, TD, kRL ? B : 4>, pcc_);
+    }
+    if (lc_ == nlev_ - 1) return lev_[lc_].xa;
+    return ((2 * degree_ - 1) & 1) ? lev_[lc_].xb : lev_[lc_].xa;
   }
 
   // Kernel launches of one V-cycle from level l.
   int vcycle_launches(int l) const {
+    if (cluster_ && l == lc_) return 1;
     if (l == nlev_ - 1) return 2;
     if (l == 1 && persist_) return 1;
     return 9 + vcycle_launches(l + 1);
@@ -465,6 +547,12 @@ class Engine : public EngineBase {
     return xo;
   }
 
+  // Chebyshev step KIND 1 or 2 on level v with operator op
+  template <int KIND, typename Op>
+  void cheb_step(const Op& op, Lev& v, const T* xo, T* xn, T c1, T c2, cudaStream_t s, const CGState* st) {
+    k_cheb<T, TD, B, KIND, Op><<<bgrid(0, v.nsl), NTB, 0, s>>>(op, v.Dinv, v.rhs, xo, xn, v.d, c1, c2, v.nsl, st);
+  }
+
   // One level of the V-cycle with the level operator `op` (assembled blocks
   // or the matrix-free fine operator).
   template <typename Op>
@@ -475,7 +563,7 @@ class Engine : public EngineBase {
     const int64_t g = bgrid(0, v.nsl);
     k_cheb<T, TD, B, 0, Op><<<g, NTB, 0, s>>>(op, v.Dinv, v.rhs, nullptr, xo, v.d, T(0), v.c2[0], v.nsl, st_);
     for (int k = 1; k < degree_; ++k) {
-      k_cheb<T, TD, B, 2, Op><<<g, NTB, 0, s>>>(op, v.Dinv, v.rhs, xo, xn, v.d, v.c1[k], v.c2[k], v.nsl, st_);
+      cheb_step<2>(op, v, xo, xn, v.c1[k], v.c2[k], s, st_);
       std::swap(xo, xn);
     }
     Lev& c = lev_[l + 1];
@@ -483,10 +571,10 @@ class Engine : public EngineBase {
     k_segsum<T, B><<<cdiv(c.n * B, 256), 256, 0, s>>>(c.child_ptr, v.S, c.rhs, c.n, st_);
     T* ec = vc(l + 1, s);
     k_prolong<T, B, OpStreams<Op>::value><<<g, NTB, 0, s>>>(v.P, v.parent, ec, xo, v.nsl, st_);
-    k_cheb<T, TD, B, 1, Op><<<g, NTB, 0, s>>>(op, v.Dinv, v.rhs, xo, xn, v.d, T(0), v.c2[0], v.nsl, st_);
+    cheb_step<1>(op, v, xo, xn, T(0), v.c2[0], s, st_);
     std::swap(xo, xn);
     for (int k = 1; k < degree_; ++k) {
-      k_cheb<T, TD, B, 2, Op><<<g, NTB, 0, s>>>(op, v.Dinv, v.rhs, xo, xn, v.d, v.c1[k], v.c2[k], v.nsl, st_);
+      cheb_step<2>(op, v, xo, xn, v.c1[k], v.c2[k], s, st_);
       std::swap(xo, xn);
     }
     return xo;
@@ -623,7 +711,7 @@ class Engine : public EngineBase {
                                  [&](cudaStream_t c) { k_noop<<<1, 1, 0, c>>>(); }, &solve_exec_, cerr) == AGG_OK;
     if (!use_cond_) {
       end_dangling_capture();
-      if (persist_) {
+      if (persist_ || cluster_) {
         err = cerr;
         return AGG_ECUDA;
       }
@@ -667,7 +755,7 @@ class Engine : public EngineBase {
   bool uses_conditional_graph() const override { return use_cond_; }
 
   int init(const HostHierarchy& h, const Mesh& m, int precision, int fine_operator, int coarse_persistent,
-           cudaStream_t s, std::string& err) override {
+           int coarse_cluster, cudaStream_t s, std::string& err) override {
     (void)precision;
     mesh_ = &m;
     perm0_ = h.lev[0].perm;
@@ -869,11 +957,13 @@ class Engine : public EngineBase {
     // well; if the runtime refuses the cooperative launch of the coarse-level
     // kernel inside a graph, the separate coarse kernels are captured instead
     persist_ = coarse_persistent && setup_persistent(err);
+    cluster_ = !persist_ && coarse_cluster && setup_cluster();
     for (;;) {
       rc = build_solve_graphs(err);
-      if (rc == AGG_OK || !persist_) break;
+      if (rc == AGG_OK || (!persist_ && !cluster_)) break;
       drop_solve_graphs();
-      persist_ = false;
+      if (persist_) persist_ = false;
+      else cluster_ = false;
     }
     if (rc) return rc;
     if (getenv("AGG_NO_COND_GRAPH")) use_cond_ = false;
@@ -1107,8 +1197,7 @@ class Engine : public EngineBase {
           break;
         case 1:
           if (use_mf0())
-            k_cheb<T, TD, B, 2, MfOpT><<<bgrid(0, n), NTB, 0, s>>>(mfop_, v.Dinv, v.rhs, v.xa, v.xb, v.d, v.c1[1],
-                                                                   v.c2[1], v.nsl, nullptr);
+            cheb_step<2>(mfop_, v, v.xa, v.xb, v.c1[1], v.c2[1], s, nullptr);
           else
             k_cheb<T, TD, B, 2, L0Op><<<bgrid(0, n), NTB, 0, s>>>(fop_, v.Dinv, v.rhs, v.xa, v.xb, v.d, v.c1[1],
                                                                   v.c2[1], v.nsl, nullptr);
@@ -1129,7 +1218,10 @@ class Engine : public EngineBase {
     return AGG_OK;
   }
 
-  void launch_counts(int& per_vcycle, int& per_iteration, int& per_setup, int& persistent) const override {
+  void launch_counts(int& per_vcycle, int& per_iteration, int& per_setup, int& persistent, int& cluster_level,
+                     int& cluster_ctas) const override {
+    cluster_level = cluster_ ? lc_ : -1;
+    cluster_ctas = cluster_ ? csize_ : 0;
     per_vcycle = vcycle_launches(0);
     per_iteration = 5 + per_vcycle;   // SpMV + (p, q), CG update, V-cycle, (r, z), p update, loop control
     per_setup = 6 + (std::is_same<T, double>::value ? 0 : 1) + per_vcycle;   // begin, residual, ||r0||, [cast], V-cycle, (r, z), p, loop control
@@ -1137,7 +1229,7 @@ class Engine : public EngineBase {
   }
 
   int kernel_cost(int id, double& bytes, double& flops) const override {
-    if (id >= 1 && id <= 3 && nlev_ < 2) return AGG_EUNSUPPORTED;
+    if (id >= 1 && id <= 4 && nlev_ < 2) return AGG_EUNSUPPORTED;
     const double n0 = (double)lev_[0].n, N = n0 * B, bb = (double)B * B;
     const double sT = sizeof(T), sD = sizeof(TD);
     const double bd = (B <= 32) ? (double)SymPad<TD, B>::NP : bb;   // stored smoother entries

@@ -504,6 +504,7 @@ static __global__ void k_segsum(const int64_t* __restrict__ child_ptr, const T* 
   const int64_t K = id / B;
   const int j = (int)(id % B);
   T s = T(0);
+#pragma unroll 4
   for (int64_t u = child_ptr[K]; u < child_ptr[K + 1]; ++u) s += S[(size_t)u * B + j];
   rc[id] = s;
 }
@@ -550,6 +551,8 @@ static __global__ void k_coarse_lower(const double* __restrict__ Linv, const T* 
   if (row >= n) return;
   const double* Lr = Linv + (size_t)row * n;
   double s = 0.0;
+  // unrolled so that several loads are in flight; the sum keeps its order
+#pragma unroll 8
   for (int64_t k = lane; k <= row; k += 32) s += Lr[k] * (double)r[k];
   s = warp_sum(s);
   if (lane == 0) y[row] = s;
@@ -564,6 +567,7 @@ static __global__ void k_coarse_upper(const double* __restrict__ U, const double
   if (row >= n) return;
   const double* Ur = U + (size_t)row * n;
   double s = 0.0;
+#pragma unroll 8
   for (int64_t k = row + lane; k < n; k += 32) s += Ur[k] * y[k];
   s = warp_sum(s);
   if (lane == 0) z[row] = (T)s;

@@ -74,6 +74,9 @@ __device__ __forceinline__ void mf_nbr_face(const MfTablesT<R>& T, const R* xn, 
 #ifndef AGG_MF2_MINB
 #define AGG_MF2_MINB 0
 #endif
+#ifndef AGG_MF2_DIRECT_BACK
+#define AGG_MF2_DIRECT_BACK 0
+#endif
 template <typename R, int B>
 struct MfOpV {
   static constexpr int kDegree = MfDegree<B>::value;
@@ -84,11 +87,21 @@ struct MfOpV {
 
   // acc += ((c M + A) x)_e for the thread's element
   __device__ __forceinline__ void apply(int64_t slice, int lane, const R* __restrict__ x, R* acc) const {
-    constexpr int P = MfDegree<B>::value, N = P + 1, Q = P + 2;
+    constexpr int N = MfDegree<B>::value + 1;
     const int64_t unit = slice * SL + lane;
     R u[N * N];
 #pragma unroll
     for (int i = 0; i < N * N; ++i) u[i] = x[(size_t)unit * B + i];
+    cell(slice, lane, u, acc);
+    faces(slice, lane, x, u, acc);
+  }
+
+  // acc += the cell (volume and mass) terms of the element whose DoFs are u;
+  // DB: back-project each Gauss point straight into acc (more FMAs, no
+  // partial sums held in registers)
+  template <bool DB = (AGG_MF2_DIRECT_BACK != 0)>
+  __device__ __forceinline__ void cell(int64_t slice, int lane, const R* u, R* acc) const {
+    constexpr int P = MfDegree<B>::value, N = P + 1, Q = P + 2;
 #ifndef AGG_MF_CELL_DIRECT
 #define AGG_MF_CELL_DIRECT 0
 #endif
@@ -142,10 +155,7 @@ struct MfOpV {
         tu[b][k] = s0;
         td[b][k] = s1;
       }
-#ifndef AGG_MF2_DIRECT_BACK
-#define AGG_MF2_DIRECT_BACK 0
-#endif
-    if constexpr (AGG_MF2_DIRECT_BACK) {
+    if constexpr (DB) {
       // back-projection of each Gauss point straight into acc (more FMAs,
       // no p0/p1 partial sums held in registers)
 #pragma unroll
@@ -213,7 +223,12 @@ struct MfOpV {
       }
     }
     }
-    // ---- face terms
+  }
+
+  // acc += the face terms of the element whose DoFs are u (x: all DoFs, for
+  // the neighbours)
+  __device__ __forceinline__ void faces(int64_t slice, int lane, const R* __restrict__ x, const R* u, R* acc) const {
+    constexpr int P = MfDegree<B>::value, N = P + 1, Q = P + 2;
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       const size_t fi = ((size_t)slice * 4 + f) * SL + lane;

@@ -1,6 +1,8 @@
-"""The persistent coarse-level kernel (agg_mg_opts.coarse_persistent: levels
->= 1 and the coarsest solve in one cooperative launch) against the separate
-per-level kernels (the default): the same
+"""The coarse-cycle kernels against the separate per-level kernels: the
+persistent kernel (agg_mg_opts.coarse_persistent: levels >= 1 and the
+coarsest solve in one cooperative launch) and the cluster kernel
+(agg_mg_opts.coarse_cluster, the default: the smallest levels and the
+coarsest solve on one thread-block cluster). The same
 V-cycle and the same PCG solve, bit for bit, in every V-cycle precision and
 for 2D and 3D blocks; fewer launches per V-cycle; and the bounded grid
 barrier: when its arrivals never come, the solve ends with AGG_ECUDA instead
@@ -26,7 +28,7 @@ def aggmg():
     return mod
 
 
-def _hier(aggmg, wl, form, env=None, persistent=True):
+def _hier(aggmg, wl, form, env=None, persistent=True, cluster=False):
     old = {}
     for k, v in (env or {}).items():
         old[k] = os.environ.get(k)
@@ -34,7 +36,7 @@ def _hier(aggmg, wl, form, env=None, persistent=True):
     try:
         fine = "mf" if form != "f64" else "bsr"
         return aggmg.Hierarchy(aggmg.Mesh.from_workload(wl), 1.0 / wl.dt, wl.maps, precision=form, fine=fine,
-                               coarse_persistent=persistent)
+                               coarse_persistent=persistent, coarse_cluster=cluster)
     finally:
         for k, v in old.items():
             if v is None:
@@ -100,3 +102,38 @@ def test_barrier_timeout_ends_the_solve_with_an_error(aggmg):
     res = h2.pcg_solve(b, x, rtol=1e-8)
     assert res["status"] == 0 and res["iterations"] > 0
     h2.close()
+
+
+CLUSTER_CASES = dict(CASES, square_q2_L2=lambda: W.jittered_square_2d(n=12, degree=2, n_levels=2),
+                     shell_q2_L4=lambda: W.ventricle_shell(16, 8, 4, n_levels=4))
+
+
+@pytest.mark.parametrize("case", list(CLUSTER_CASES))
+@pytest.mark.parametrize("form", ["f64", "f32", "bf16s"])
+def test_cluster_kernel_equals_separate_kernels_bitwise(aggmg, case, form):
+    wl = CLUSTER_CASES[case]()
+    hc = _hier(aggmg, wl, form, persistent=False, cluster=True)
+    hs = _hier(aggmg, wl, form, persistent=False, cluster=False)
+    lc, ls = hc.launches(), hs.launches()
+    assert ls["cluster_level"] == -1 and not ls["persistent"]
+    assert lc["cluster_level"] >= 1 and lc["cluster_ctas"] in (8, 16)
+    L = wl.n_levels
+    assert ls["per_vcycle"] == 9 * (L - 1) + 2
+    assert lc["per_vcycle"] == 9 * lc["cluster_level"] + 1
+    n = wl.n_dofs
+    rng = np.random.default_rng(12)
+    r = torch.tensor(rng.standard_normal(n), dtype=torch.float64, device="cuda")
+    zc, zs = torch.empty_like(r), torch.empty_like(r)
+    for _ in range(2):
+        hc.vcycle_apply(r, zc)
+        hs.vcycle_apply(r, zs)
+        torch.cuda.synchronize()
+        assert torch.equal(zc, zs), float((zc - zs).abs().max())
+    b = torch.tensor(rng.standard_normal(n), dtype=torch.float64, device="cuda")
+    xc, xs = torch.zeros_like(b), torch.zeros_like(b)
+    rc = hc.pcg_solve(b, xc, rtol=1e-10, flexible=(form != "f64"))
+    rs = hs.pcg_solve(b, xs, rtol=1e-10, flexible=(form != "f64"))
+    assert rc["iterations"] == rs["iterations"]
+    assert torch.equal(xc, xs)
+    hc.close()
+    hs.close()
