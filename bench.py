@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--fine", default=None, choices=["bsr", "mf"],
                     help="V-cycle level-0 operator: assembled blocks or matrix-free "
                          "(default: matrix-free for float32 V-cycles on quadrilaterals of p <= 3 "
-                         "and hexahedra of p <= 2, assembled otherwise)")
+                         "and hexahedra of p <= 3, assembled otherwise)")
     ap.add_argument("--workload", default="jsquare2d", choices=list(WORKLOADS))
     ap.add_argument("--n", type=int, default=None, help="elements per direction (box workloads)")
     ap.add_argument("--agglomeration", default="blocks", choices=["blocks", "rtree"],
@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=10,
                     help="also time this many steps of the plain float64 form (float64 V-cycle) from the "
                          "timed region's starting state, in the same run (0: skip)")
+    ap.add_argument("--cheb-range", type=float, default=None,
+                    help="Chebyshev lambda_max / lambda_min of the smoother (default: the library's)")
+    ap.add_argument("--cheb-safety", type=float, default=None,
+                    help="lambda_max = safety * Lanczos estimate (default: the library's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-kernel", type=int, default=None,
                     help="set up, launch kernel id K three times (for ncu) and exit")
@@ -165,7 +169,7 @@ if {rtree_M}:
 disc = sipg.assemble(wl.mesh.vertices, wl.mesh.elements, wl.conductivity, wl.degree, wl.penalty_mode,
                      wl.penalty_coeff)
 opts = md.StepOptions(dt=wl.dt, ionic=wl.ionic, rtol=wl.rtol, iapp_value=wl.iapp_value, iapp_steps=wl.iapp_steps)
-h = mg.build_hierarchy(disc, opts.mass_coeff(), wl.maps)
+h = mg.build_hierarchy(disc, opts.mass_coeff(), wl.maps, cheb_range=wl.cheb_range)
 u = np.zeros(disc.n); w = np.repeat(W.resting_gates(wl.ionic)[:, None], disc.n, axis=1)
 if w.shape[0] == 1: w = w[0]
 mask = wl.stim_mask_nodal()
@@ -295,14 +299,17 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda")
     wl = workload(args)
     if args.fine is None:
-        mf_ok = wl.degree <= (3 if wl.mesh.dim == 2 else 2)
+        mf_ok = wl.degree <= 3
         args.fine = "mf" if (args.form != "f64" and mf_ok) else "bsr"
     t0 = time.time()
     mesh = aggmg.Mesh.from_workload(wl, adjoint_data=args.adjoint_steps > 0)
     if args.agglomeration == "rtree":                # nested agglomerates from the mesh's R*-tree
         import dataclasses
         wl = dataclasses.replace(wl, maps=aggmg.rtree_maps(mesh, args.max_entries))
-    hier = aggmg.Hierarchy(mesh, 1.0 / wl.dt, wl.maps, precision=args.form, fine=args.fine)
+    if args.cheb_range is None:
+        args.cheb_range = wl.cheb_range
+    cheb = {k: v for k, v in (("cheb_range", args.cheb_range), ("safety", args.cheb_safety)) if v is not None}
+    hier = aggmg.Hierarchy(mesh, 1.0 / wl.dt, wl.maps, precision=args.form, fine=args.fine, **cheb)
     setup_s = time.time() - t0
     if args.profile_kernel is not None:
         hier.profile_kernel(args.profile_kernel, 3)
@@ -363,7 +370,7 @@ def run_ours(args, rank, world):
     # one run shows both forms at the same 1e-8 relative residual
     fp64 = None
     if args.form != "f64" and args.fp64_steps > 0:
-        h64 = aggmg.Hierarchy(mesh, 1.0 / wl.dt, wl.maps, precision="f64", fine="bsr")
+        h64 = aggmg.Hierarchy(mesh, 1.0 / wl.dt, wl.maps, precision="f64", fine="bsr", **cheb)
         s64 = aggmg.Monodomain(h64, wl.dt, wl.ionic, iapp_mask=mask, iapp_value=wl.iapp_value,
                                iapp_steps=wl.iapp_steps, rtol=wl.rtol, flexible=False)
         u64, w64 = u_start.clone(), w_start.clone()
@@ -583,7 +590,7 @@ def run_reference(args, rank):
                          wl.penalty_coeff)
     full = md.StepOptions(dt=wl.dt, ionic=wl.ionic, rtol=wl.rtol, iapp_value=wl.iapp_value,
                           iapp_steps=wl.iapp_steps)
-    h = mg.build_hierarchy(disc, full.mass_coeff(), wl.maps)
+    h = mg.build_hierarchy(disc, full.mass_coeff(), wl.maps, cheb_range=wl.cheb_range)
     u = np.zeros(disc.n)
     w = np.repeat(W.resting_gates(wl.ionic)[:, None], disc.n, axis=1)
     if w.shape[0] == 1:

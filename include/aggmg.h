@@ -127,7 +127,7 @@ typedef struct {
                                     mass term evaluated from quadrature data
                                     with sum factorisation, Section 5.2); 1
                                     needs quadrilaterals with p <= 3 or
-                                    hexahedra with p <= 2 whose neighbours
+                                    hexahedra with p <= 3 whose neighbours
                                     list each shared face's corners in the
                                     same order, quad_extra 1 and a float32
                                     V-cycle, else AGG_EUNSUPPORTED. The outer

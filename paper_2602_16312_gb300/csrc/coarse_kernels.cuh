@@ -46,57 +46,23 @@ struct RowLane {
   }
 };
 
-// (A x)_r of the lane's unit. The row's blocks are taken RL_GROUP at a time:
-// the column ids, block entries and neighbour values of a group are loaded
-// unconditionally (indices past the row's end clamped to its first block)
-// before any of them is used, so their latencies overlap instead of forming a
-// chain of dependent loads per block; the sum then adds the valid blocks in
-// row order, as one block at a time would. (Loading ids together and
-// broadcasting them by warp shuffles, under a per-block branch, measured
-// slower on GB300: 16.6 against 11.8 us per level-1 Chebyshev step.)
-#ifndef AGG_RL_GROUP
-#define AGG_RL_GROUP 1
-#endif
+// (A x)_r of the lane's unit. Two ways to overlap the per-block chain of
+// loads (column id, then the neighbour's values) measured no faster on
+// GB300: ids loaded together and broadcast by warp shuffles (16.6 against
+// 11.8 us per level-1 Chebyshev step), and groups of 2-4 blocks loaded
+// unconditionally before use (V-cycle 598-603 against 596 us in 2D, 3.3-4.3
+// against 3.1 ms on the shell).
 template <typename T, int B>
 __device__ __forceinline__ T rl_row(const CsrBlocks<T>& A, const RowLane<B>& L, const T* __restrict__ x) {
-  constexpr int G = AGG_RL_GROUP;
   T s = T(0);
   if (!L.active) return s;
   const int j0 = A.rowptr[L.unit], j1 = A.rowptr[L.unit + 1];
-  if constexpr (G == 1) {
-    for (int j = j0; j < j1; ++j) {
-      const int col = A.cols[j];
-      const T* blk = A.vals + (size_t)j * B * B + L.r;
-      const T* xb = x + (size_t)col * B;
+  for (int j = j0; j < j1; ++j) {
+    const int col = A.cols[j];
+    const T* blk = A.vals + (size_t)j * B * B + L.r;
+    const T* xb = x + (size_t)col * B;
 #pragma unroll
-      for (int c = 0; c < B; ++c) s += blk[c * B] * xb[c];
-    }
-  } else {
-    for (int jb = j0; jb < j1; jb += G) {
-      int jj[G], col[G];
-#pragma unroll
-      for (int t = 0; t < G; ++t) {
-        jj[t] = (jb + t < j1) ? jb + t : j0;
-        col[t] = A.cols[jj[t]];
-      }
-      T bv[G][B], xv[G][B];
-#pragma unroll
-      for (int t = 0; t < G; ++t) {
-        const T* blk = A.vals + (size_t)jj[t] * B * B + L.r;
-        const T* xb = x + (size_t)col[t] * B;
-#pragma unroll
-        for (int c = 0; c < B; ++c) {
-          bv[t][c] = blk[c * B];
-          xv[t][c] = xb[c];
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < G; ++t)
-        if (jb + t < j1) {
-#pragma unroll
-          for (int c = 0; c < B; ++c) s += bv[t][c] * xv[t][c];
-        }
-    }
+    for (int c = 0; c < B; ++c) s += blk[c * B] * xb[c];
   }
   return s;
 }

@@ -53,7 +53,7 @@ class Engine : public EngineBase {
   // matrix-free fine operator: float32 V-cycle on quadrilaterals of p = 1..3
   // and hexahedra of p = 1, 2
   static constexpr bool kMf =
-      std::is_same<T, float>::value && (B == 4 || B == 9 || B == 16 || B == 8 || B == 27);
+      std::is_same<T, float>::value && (B == 4 || B == 9 || B == 16 || B == 8 || B == 27 || B == 64);
   using MfOpT = typename std::conditional<kMf, typename MfOpFor<kMf ? B : 9>::type, SellOp<T, B>>::type;
   bool mf_ = false;
   MfOpT mfop_{};
@@ -930,7 +930,7 @@ class Engine : public EngineBase {
         mf_bytes_ = (int64_t)(md.cell.size() * 4 + md.face.size() * 4 + md.nbr.size() * 4 + md.code.size());
         mf_ = true;
       } else {
-        err = "the matrix-free fine operator needs quadrilaterals of p <= 3 or hexahedra of p <= 2 and a float32 V-cycle";
+        err = "the matrix-free fine operator needs quadrilaterals or hexahedra of p <= 3 and a float32 V-cycle";
         return AGG_EUNSUPPORTED;
       }
     }

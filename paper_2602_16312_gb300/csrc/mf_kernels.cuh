@@ -309,6 +309,7 @@ struct MfOpV {
 template <int B> struct Mf3Degree;
 template <> struct Mf3Degree<8> { static constexpr int value = 1; };
 template <> struct Mf3Degree<27> { static constexpr int value = 2; };
+template <> struct Mf3Degree<64> { static constexpr int value = 3; };
 
 #ifndef AGG_MF3_MINB
 #define AGG_MF3_MINB 0
@@ -548,6 +549,7 @@ template <int B> using MfOp3 = MfOp3V<float, B>;
 template <typename R, int B> struct MfOpForT { using type = MfOpV<R, B>; };
 template <typename R> struct MfOpForT<R, 8> { using type = MfOp3V<R, 8>; };
 template <typename R> struct MfOpForT<R, 27> { using type = MfOp3V<R, 27>; };
+template <typename R> struct MfOpForT<R, 64> { using type = MfOp3V<R, 64>; };
 template <int B> struct MfOpFor { using type = typename MfOpForT<float, B>::type; };
 
 // Sliced block-sparse operator in the same interface.

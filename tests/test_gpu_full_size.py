@@ -51,6 +51,7 @@ CONFIGS = {
                             2.0),
     "shell_q2_128x96x16_f32": ("W.ventricle_shell()", "f32", "mf", (4, 4, 1), 3.0),
     "cube3d_q3_48_f64": ("W.cube_3d_adjoint(n=48)", "f64", "bsr", (4, 4, 4), 3.0),
+    "cube3d_q3_48_f32": ("W.cube_3d_adjoint(n=48)", "f32", "mf", (4, 4, 4), 3.0),
 }
 
 
@@ -81,7 +82,7 @@ def test_full_size_every_row(name):
     c = 1.0 / wl.dt
     rng = np.random.default_rng(91)
     mesh = aggmg.Mesh.from_workload(wl)
-    hier = aggmg.Hierarchy(mesh, c, wl.maps, precision=form, fine=fine)
+    hier = aggmg.Hierarchy(mesh, c, wl.maps, precision=form, fine=fine, cheb_range=wl.cheb_range)
 
     # ---- the two level-0 operators on a seeded vector
     x = rng.standard_normal(N)
@@ -150,7 +151,7 @@ def bench_oracle_trajectory():
     wl = W.jittered_square_2d(n=512, degree=2, n_levels=4)
     disc = osipg.assemble(wl.mesh.vertices, wl.mesh.elements, wl.conductivity, wl.degree, wl.penalty_mode,
                           wl.penalty_coeff)
-    ho = omg.build_hierarchy(disc, 1.0 / wl.dt, wl.maps)
+    ho = omg.build_hierarchy(disc, 1.0 / wl.dt, wl.maps, cheb_range=wl.cheb_range)
     opts = omd.StepOptions(dt=wl.dt, ionic=wl.ionic, rtol=wl.rtol, iapp_value=wl.iapp_value,
                            iapp_steps=wl.iapp_steps)
     u, w = np.zeros(disc.n), np.zeros(disc.n)
@@ -171,7 +172,7 @@ def test_bench_workload_trajectory_matches_oracle(bench_oracle_trajectory, form)
     fine = "mf" if form == "f32" else "bsr"
     steps = TRAJ_STEPS if form == "f32" else 3
     mesh = aggmg.Mesh.from_workload(wl)
-    hier = aggmg.Hierarchy(mesh, 1.0 / wl.dt, wl.maps, precision=form, fine=fine)
+    hier = aggmg.Hierarchy(mesh, 1.0 / wl.dt, wl.maps, precision=form, fine=fine, cheb_range=wl.cheb_range)
     mask = _dev(wl.stim_mask_nodal())
     sim = aggmg.Monodomain(hier, wl.dt, wl.ionic, iapp_mask=mask, iapp_value=wl.iapp_value,
                            iapp_steps=wl.iapp_steps, rtol=wl.rtol, flexible=(form == "f32"))
