@@ -48,6 +48,7 @@ import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
 
+from . import direct_coarse
 from . import refelem as re
 from .sipg import nodal_points
 
@@ -199,13 +200,18 @@ def point_jacobi_blocks(A, B):
 
 
 def build_hierarchy(disc, mass_coeff, maps, block_jacobi=True, lanczos_steps=12,
-                    safety=1.2, cheb_range=20.0, degree=3):
-    """Algorithm 3 (GenerateCoarserOperators) plus the smoother set-up."""
+                    safety=1.2, cheb_range=20.0, degree=3, direct=None):
+    """Algorithm 3 (GenerateCoarserOperators) plus the smoother set-up.
+    direct = dict(D=conductivity (E, d, d), c_pen=C_pen[, quad_extra=1])
+    assembles the coarse operators on the agglomerates instead of the
+    Galerkin products (the non-inherited operators of Section 5.1,
+    oracle.direct_coarse); None keeps the inherited ones."""
     A0 = disc.A0(mass_coeff)
     p, B = disc.p, disc.B
     levels = [Level(A=A0, n_units=disc.n_elements, B=B)]
     y = nodal_points(disc.vertices, disc.elements, p)
     lo = hi = None
+    unit = np.arange(disc.n_elements, dtype=np.int64)      # fine element -> unit of the current level
     for l, amap in enumerate(maps):
         amap = np.asarray(amap, dtype=np.int64)
         if l == 0:
@@ -214,7 +220,12 @@ def build_hierarchy(disc, mass_coeff, maps, block_jacobi=True, lanczos_steps=12,
             lo, hi = coarser_boxes(lo, hi, amap)
         P = prolongation(y, amap, lo, hi, p)
         levels[l].P = P
-        Ac = galerkin(levels[l].A, P)
+        unit = amap[unit]
+        if direct is None:
+            Ac = galerkin(levels[l].A, P)
+        else:
+            Ac = direct_coarse.level_operator(disc.vertices, disc.elements, direct["D"], p, mass_coeff,
+                                              direct["c_pen"], unit, lo, hi, direct.get("quad_extra", 1))
         levels.append(Level(A=Ac, n_units=int(amap.max()) + 1, B=B, lo=lo, hi=hi))
         y = box_nodal_points(lo, hi, p)
     for lev in levels[:-1]:
