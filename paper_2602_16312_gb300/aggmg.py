@@ -40,7 +40,8 @@ class MGOpts(C.Structure):
     _fields_ = [("n_levels", C.c_int), ("agg_maps", C.POINTER(C.POINTER(C.c_int32))),
                 ("smoother_degree", C.c_int), ("block_jacobi", C.c_int), ("lanczos_steps", C.c_int),
                 ("cheb_upper_safety", C.c_double), ("cheb_range", C.c_double), ("vcycle_precision", C.c_int),
-                ("fine_operator", C.c_int), ("coarse_persistent", C.c_int), ("coarse_cluster", C.c_int)]
+                ("fine_operator", C.c_int), ("coarse_persistent", C.c_int), ("coarse_cluster", C.c_int),
+                ("coarse_operator", C.c_int)]
 
 
 class PCGOpts(C.Structure):
@@ -258,7 +259,8 @@ FINE_OPERATORS = {"bsr": 0, "mf": 1}
 
 
 def _mg_opts(maps: Sequence[np.ndarray], precision="f64", block_jacobi=True, lanczos_steps=12,
-             safety=1.2, cheb_range=20.0, fine="bsr", coarse_persistent=False, coarse_cluster=False):
+             safety=1.2, cheb_range=20.0, fine="bsr", coarse_persistent=False, coarse_cluster=False,
+             coarse_operator="inherited"):
     o = MGOpts()
     lib().agg_mg_opts_default(C.byref(o))
     keep = [np.ascontiguousarray(m, dtype=np.int32) for m in maps]
@@ -275,6 +277,8 @@ def _mg_opts(maps: Sequence[np.ndarray], precision="f64", block_jacobi=True, lan
     o.fine_operator = FINE_OPERATORS[fine] if isinstance(fine, str) else int(fine)
     o.coarse_persistent = int(coarse_persistent)
     o.coarse_cluster = int(coarse_cluster)
+    o.coarse_operator = {"inherited": 0, "direct": 1}[coarse_operator] if isinstance(coarse_operator, str) \
+        else int(coarse_operator)
     return o, (keep, arr)
 
 

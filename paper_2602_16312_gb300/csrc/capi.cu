@@ -221,6 +221,7 @@ void agg_mg_opts_default(agg_mg_opts* o) {
   o->fine_operator = 0;
   o->coarse_persistent = 0;
   o->coarse_cluster = 0;
+  o->coarse_operator = 0;
 }
 
 static agg_status check_mg_opts(const agg_mg_opts* o, double mass_coeff);
@@ -305,6 +306,7 @@ static agg_status check_mg_opts(const agg_mg_opts* o, double mass_coeff) {
   if (o->fine_operator != 0 && o->fine_operator != 1) return fail(AGG_EINVAL, "fine_operator");
   if (o->coarse_persistent != 0 && o->coarse_persistent != 1) return fail(AGG_EINVAL, "coarse_persistent");
   if (o->coarse_cluster != 0 && o->coarse_cluster != 1) return fail(AGG_EINVAL, "coarse_cluster");
+  if (o->coarse_operator != 0 && o->coarse_operator != 1) return fail(AGG_EINVAL, "coarse_operator");
   return AGG_OK;
 }
 
@@ -317,6 +319,7 @@ static HierOptions host_options(const agg_mg_opts* o) {
   ho.lanczos_steps = o->lanczos_steps;
   ho.safety = o->cheb_upper_safety;
   ho.range = o->cheb_range;
+  ho.direct = o->coarse_operator == 1;
   return ho;
 }
 

@@ -391,8 +391,8 @@ static __global__ void __launch_bounds__(UnitThreads<B>::value)
 #pragma unroll
   for (int r = 0; r < B; ++r) t[r] = 0.0;
   block_mv<double, double, B>(Minv + (size_t)slice * SL * KP, lane, A0u + o, t);
-#pragma unroll
   const int ng = ionic_gates(prm.model);
+#pragma unroll
   for (int r = 0; r < B; ++r) {
     const double ur = u[o + r];
     double g[kMaxGates], H[kMaxGates], I;

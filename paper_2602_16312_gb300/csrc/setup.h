@@ -107,10 +107,23 @@ struct HierOptions {
   bool block_jacobi = true;
   int lanczos_steps = 12;
   double safety = 1.2, range = 20.0;
+  bool direct = false;                 // non-inherited coarse operators (setup_direct.cpp)
 };
 
 int hierarchy_build(const Mesh& m, double mass_coeff, const HierOptions& o, HostHierarchy& h,
                     std::string& err);
+
+// Multilinear element map from the 2^dim corners Xc (corner c has bit k = 1
+// at xi_k = 1): x(xi) and J[k][l] = dx_k / dxi_l (setup_mesh.cpp).
+void map_point(int dim, const double* Xc, const double* xi, double* x, double J[3][3]);
+// Determinant of J (dim 2 or 3) and its inverse Ji.
+double det_inv(int dim, double J[3][3], double Ji[3][3]);
+
+// c M_l + A_l assembled directly on the agglomerates of level l >= 1 (the
+// non-inherited operator of Section 5.1), block rows in level l's internal
+// order; needs the levels' parents and level l's boxes.
+int direct_level_build(const Mesh& m, const HostHierarchy& h, int l, double mass_coeff, BlockCSR& out,
+                       std::string& err);
 
 // Quadrature data of the matrix-free fine operator, elements in the
 // order `perm` (internal -> element id), packed per slice of 32 elements:

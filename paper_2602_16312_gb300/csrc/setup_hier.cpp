@@ -288,48 +288,53 @@ int hierarchy_build(const Mesh& m, double c, const HierOptions& o, HostHierarchy
         }
       }
     }
-    // Galerkin product, one coarse block row per thread
-    std::vector<std::vector<int32_t>> rcols(lc.n);
-    std::vector<std::vector<double>> rvals(lc.n);
+    if (o.direct) {
+      int rc = direct_level_build(m, h, l + 1, c, lc.A, err);
+      if (rc) return rc;
+    } else {
+      // Galerkin product, one coarse block row per thread
+      std::vector<std::vector<int32_t>> rcols(lc.n);
+      std::vector<std::vector<double>> rvals(lc.n);
 #pragma omp parallel for schedule(dynamic, 4)
-    for (int64_t K = 0; K < lc.n; ++K) {
-      std::vector<int32_t> cols;
-      std::vector<double> acc;
-      std::vector<double> T((size_t)B * B);
-      for (int64_t u = lc.child_ptr[K]; u < lc.child_ptr[K + 1]; ++u) {
-        const double* Pu = &lf.P[(size_t)u * B * B];
-        for (int64_t k = lf.A.rowptr[u]; k < lf.A.rowptr[u + 1]; ++k) {
-          const int64_t v = lf.A.col[k];
-          const int32_t Kp = lf.parent[v];
-          size_t slot = 0;
-          while (slot < cols.size() && cols[slot] != Kp) ++slot;
-          if (slot == cols.size()) {
-            cols.push_back(Kp);
-            acc.resize(acc.size() + (size_t)B * B, 0.0);
+      for (int64_t K = 0; K < lc.n; ++K) {
+        std::vector<int32_t> cols;
+        std::vector<double> acc;
+        std::vector<double> T((size_t)B * B);
+        for (int64_t u = lc.child_ptr[K]; u < lc.child_ptr[K + 1]; ++u) {
+          const double* Pu = &lf.P[(size_t)u * B * B];
+          for (int64_t k = lf.A.rowptr[u]; k < lf.A.rowptr[u + 1]; ++k) {
+            const int64_t v = lf.A.col[k];
+            const int32_t Kp = lf.parent[v];
+            size_t slot = 0;
+            while (slot < cols.size() && cols[slot] != Kp) ++slot;
+            if (slot == cols.size()) {
+              cols.push_back(Kp);
+              acc.resize(acc.size() + (size_t)B * B, 0.0);
+            }
+            gemm(&lf.A.val[(size_t)k * B * B], &lf.P[(size_t)v * B * B], T.data(), B);
+            gemm_tn_acc(Pu, T.data(), &acc[slot * B * B], B);
           }
-          gemm(&lf.A.val[(size_t)k * B * B], &lf.P[(size_t)v * B * B], T.data(), B);
-          gemm_tn_acc(Pu, T.data(), &acc[slot * B * B], B);
+        }
+        std::vector<int> ord(cols.size());
+        std::iota(ord.begin(), ord.end(), 0);
+        std::sort(ord.begin(), ord.end(), [&](int a, int b) { return cols[a] < cols[b]; });
+        rcols[K].resize(cols.size());
+        rvals[K].resize(acc.size());
+        for (size_t s = 0; s < ord.size(); ++s) {
+          rcols[K][s] = cols[ord[s]];
+          std::memcpy(&rvals[K][s * B * B], &acc[(size_t)ord[s] * B * B], sizeof(double) * B * B);
         }
       }
-      std::vector<int> ord(cols.size());
-      std::iota(ord.begin(), ord.end(), 0);
-      std::sort(ord.begin(), ord.end(), [&](int a, int b) { return cols[a] < cols[b]; });
-      rcols[K].resize(cols.size());
-      rvals[K].resize(acc.size());
-      for (size_t s = 0; s < ord.size(); ++s) {
-        rcols[K][s] = cols[ord[s]];
-        std::memcpy(&rvals[K][s * B * B], &acc[(size_t)ord[s] * B * B], sizeof(double) * B * B);
+      lc.A.nrows = lc.n;
+      lc.A.B = B;
+      lc.A.rowptr.assign(lc.n + 1, 0);
+      for (int64_t K = 0; K < lc.n; ++K) lc.A.rowptr[K + 1] = lc.A.rowptr[K] + (int64_t)rcols[K].size();
+      lc.A.col.resize(lc.A.rowptr[lc.n]);
+      lc.A.val.resize((size_t)lc.A.rowptr[lc.n] * B * B);
+      for (int64_t K = 0; K < lc.n; ++K) {
+        std::copy(rcols[K].begin(), rcols[K].end(), lc.A.col.begin() + lc.A.rowptr[K]);
+        std::copy(rvals[K].begin(), rvals[K].end(), lc.A.val.begin() + lc.A.rowptr[K] * B * B);
       }
-    }
-    lc.A.nrows = lc.n;
-    lc.A.B = B;
-    lc.A.rowptr.assign(lc.n + 1, 0);
-    for (int64_t K = 0; K < lc.n; ++K) lc.A.rowptr[K + 1] = lc.A.rowptr[K] + (int64_t)rcols[K].size();
-    lc.A.col.resize(lc.A.rowptr[lc.n]);
-    lc.A.val.resize((size_t)lc.A.rowptr[lc.n] * B * B);
-    for (int64_t K = 0; K < lc.n; ++K) {
-      std::copy(rcols[K].begin(), rcols[K].end(), lc.A.col.begin() + lc.A.rowptr[K]);
-      std::copy(rvals[K].begin(), rvals[K].end(), lc.A.val.begin() + lc.A.rowptr[K] * B * B);
     }
     // nodal points of level l+1: GLL nodes of the boxes
     lc.nodes.resize((size_t)lc.n * B * dim);

@@ -127,6 +127,8 @@ void tensor_basis(const Tables1D& t, int dim, const double* xi, Basis& out) {
   }
 }
 
+}  // namespace
+
 // multilinear map: x(xi) and J[k][l] = dx_k/dxi_l from the 2^dim corners
 void map_point(int dim, const double* Xc, const double* xi, double* x, double J[MAXD][MAXD]) {
   int V = 1 << dim;
@@ -176,6 +178,8 @@ double det_inv(int dim, double J[MAXD][MAXD], double Ji[MAXD][MAXD]) {
   Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
   return det;
 }
+
+namespace {
 
 // physical gradient: component k = sum_l Jinv[l][k] * ghat_l
 inline void phys_grad(int dim, const double Ji[MAXD][MAXD], const double* gh, double* g) {
