@@ -61,6 +61,8 @@ def parse():
                     help="Chebyshev lambda_max / lambda_min of the smoother (default: the library's)")
     ap.add_argument("--cheb-safety", type=float, default=None,
                     help="lambda_max = safety * Lanczos estimate (default: the library's)")
+    ap.add_argument("--coarse-operator", default="inherited", choices=["inherited", "direct"],
+                    help="coarse operators: Galerkin products (inherited) or assembled on the agglomerates")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-kernel", type=int, default=None,
                     help="set up, launch kernel id K three times (for ncu) and exit")
@@ -84,7 +86,11 @@ WORKLOADS = {
 # (bytes, sha256 prefix of the kernel sources the capture ran). A stored figure
 # is reported only while the kernel sources still hash to the captured value;
 # after any change to them, and for other configurations, traffic is null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # 512x512 Q2 square, float32 V-cycle, matrix-free level 0: the Chebyshev step
+    # (235.0 MB read + 3.7 MB written; ncu --set full, first of three launches)
+    ("jsquare2d_q2_512x512", "f32", "mf", "blocks", 1): (238_678_016.0, "32e5e4620fd26529"),
+}
 
 
 def kernel_sources_hash(fine):
@@ -309,7 +315,8 @@ def run_ours(args, rank, world):
     if args.cheb_range is None:
         args.cheb_range = wl.cheb_range
     cheb = {k: v for k, v in (("cheb_range", args.cheb_range), ("safety", args.cheb_safety)) if v is not None}
-    hier = aggmg.Hierarchy(mesh, 1.0 / wl.dt, wl.maps, precision=args.form, fine=args.fine, **cheb)
+    hier = aggmg.Hierarchy(mesh, 1.0 / wl.dt, wl.maps, precision=args.form, fine=args.fine,
+                           coarse_operator=args.coarse_operator, **cheb)
     setup_s = time.time() - t0
     if args.profile_kernel is not None:
         hier.profile_kernel(args.profile_kernel, 3)
@@ -370,7 +377,8 @@ def run_ours(args, rank, world):
     # one run shows both forms at the same 1e-8 relative residual
     fp64 = None
     if args.form != "f64" and args.fp64_steps > 0:
-        h64 = aggmg.Hierarchy(mesh, 1.0 / wl.dt, wl.maps, precision="f64", fine="bsr", **cheb)
+        h64 = aggmg.Hierarchy(mesh, 1.0 / wl.dt, wl.maps, precision="f64", fine="bsr",
+                              coarse_operator=args.coarse_operator, **cheb)
         s64 = aggmg.Monodomain(h64, wl.dt, wl.ionic, iapp_mask=mask, iapp_value=wl.iapp_value,
                                iapp_steps=wl.iapp_steps, rtol=wl.rtol, flexible=False)
         u64, w64 = u_start.clone(), w_start.clone()
@@ -513,6 +521,7 @@ def run_ours(args, rank, world):
         "mdof_per_s": N * total_steps / t / 1e6,
         "config": bench_config(wl, args),
         "solver": {"form": args.form, "fine_operator": args.fine, "parallelism": f"replicas x{world}",
+                   "coarse_operator": args.coarse_operator,
                    "coarse_levels": ("one persistent kernel" if lc["persistent"] else
                                      f"separate kernels; levels >= {lc['cluster_level']} and the coarsest solve "
                                      f"on one {lc['cluster_ctas']}-CTA cluster" if lc["cluster_level"] >= 0

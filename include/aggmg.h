@@ -227,9 +227,8 @@ agg_status agg_vcycle_apply(agg_hier_t hier, const double* r_dev, double* z_dev,
 /* ------------------------------------------------------------------ allocation-free product
  * agg_operator_apply_static: the same product y = A_l x as agg_operator_apply
  * (same operator, same kernels, same results), for callers that must not
- * allocate device memory at the time of the call: code running while a CUDA
- * stream is captured into a graph (allocation is not allowed inside a
- * capture), or an embedding that fixes its device-memory budget at start-up.
+ * allocate device memory at the time of the call, such as an embedding that
+ * fixes its device-memory budget at start-up.
  * It has no counterpart in the paper: it only changes where the two
  * temporary, unit-permuted copies of x and y live.
  *
@@ -239,8 +238,8 @@ agg_status agg_vcycle_apply(agg_hier_t hier, const double* r_dev, double* z_dev,
  * routine. Levels 0 .. n_levels-2 only; a level whose padded vector length
  * ((units rounded up to 32) * (p+1)^d) exceeds AGG_STATIC_APPLY_MAX_ENTRIES
  * returns AGG_EINVAL. The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress, once per device, with that device current);
- * make that first call before any stream capture. The address is kept for
+ * address (cudaGetSymbolAddress, once per device, with that device current).
+ * The address is kept for
  * the life of the process, so resetting the device (cudaDeviceReset) or
  * destroying its primary context after the first call is not supported
  * while the library stays loaded. The array is shared by all calls and keeps

@@ -1,9 +1,8 @@
 """agg_operator_apply_static against agg_operator_apply, through the C ABI.
 
 The static variant exists for callers that may not allocate device memory
-while they run (for example code that executes inside a CUDA stream capture,
-where allocation is not allowed, or an embedding whose device-memory budget
-is fixed after start-up). It must give the same product as the allocating
+while they run (for example an embedding whose device-memory budget is fixed
+after start-up). It must give the same product as the allocating
 entry point, call after call, since it reuses one static scratch array.
 This file sorts last so that a stop-at-first-failure run has already run
 every other test.
