@@ -68,3 +68,27 @@ def test_static_apply_rejects_levels_beyond_its_maximum(aggmg):
     torch.cuda.synchronize()
     assert torch.equal(y1, y1r)
     hier.close()
+
+
+def test_static_apply_leaves_free_device_memory_unchanged(aggmg):
+    """After the first call, repeated static products on every level leave the
+    device's free memory (cudaMemGetInfo) exactly where it was."""
+    wl = W.jittered_square_2d(n=30, n_levels=3)
+    hier = aggmg.Hierarchy(aggmg.Mesh.from_workload(wl), 1.0 / wl.dt, wl.maps, precision="f64")
+    B = (wl.degree + 1) ** 2
+    units = hier.stats()["units"]
+    bufs = []
+    for level in range(hier.n_levels - 1):
+        n = units[level] * B
+        bufs.append((level, torch.ones(n, dtype=torch.float64, device="cuda"),
+                     torch.empty(n, dtype=torch.float64, device="cuda")))
+    for level, x, y in bufs:
+        hier.operator_apply_static(level, x, y)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(10):
+        for level, x, y in bufs:
+            hier.operator_apply_static(level, x, y)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    hier.close()
