@@ -50,6 +50,10 @@ template <typename T, typename TD, int B>
 class Engine : public EngineBase {
   static constexpr int NTB = UnitThreads<B>::value;
   static constexpr bool kRL = (B <= 32);
+  // coarse levels on the row-lane kernels: warp-shuffle units (B <= 32, kRL;
+  // also eligible for the persistent and cluster kernels) or shared-memory
+  // units (B = 64)
+  static constexpr bool kRowLanes = kRL || B == 64;
   // matrix-free fine operator: float32 V-cycle on quadrilaterals of p = 1..3
   // and hexahedra of p = 1, 2
   static constexpr bool kMf =
@@ -359,6 +363,8 @@ class Engine : public EngineBase {
     }
     if constexpr (kRL) {
       if (l == 1 && persist_) return launch_persistent(s);
+    }
+    if constexpr (kRowLanes) {
       if (l > 0) return vc_rowlane(l, s);
     }
     if (l == 0) return vc_level(l, fop_, s);
@@ -514,12 +520,25 @@ class Engine : public EngineBase {
     return ((2 * degree_ - 1) & 1) ? lev_[lc_].xb : lev_[lc_].xa;
   }
 
-  // Kernel launches of one V-cycle from level l.
+  // Whether level l's first smoother step sums the finer level's
+  // restriction itself (k_rl_cheb_restricted) instead of a k_segsum launch:
+  // the row-lane levels run as separate kernels.
+  bool fused_restrict(int l) const {
+    if constexpr (!kRowLanes) return false;
+    if (l < 1 || l >= nlev_ - 1) return false;
+    if (l == 1 && persist_) return false;
+    if (cluster_ && l >= lc_) return false;
+    return true;
+  }
+
+  // Kernel launches of one V-cycle from level l: 2 degree smoother steps,
+  // residual + restriction, segmented sum (unless the next level fuses it),
+  // prolongation.
   int vcycle_launches(int l) const {
     if (cluster_ && l == lc_) return 1;
     if (l == nlev_ - 1) return 2;
     if (l == 1 && persist_) return 1;
-    return 9 + vcycle_launches(l + 1);
+    return 2 * degree_ + 3 - (fused_restrict(l + 1) ? 1 : 0) + vcycle_launches(l + 1);
   }
 
   // One coarse level (l >= 1) with the row-lane kernels.
@@ -527,15 +546,20 @@ class Engine : public EngineBase {
     Lev& v = lev_[l];
     T* xo = v.xa;
     T* xn = v.xb;
-    const int64_t g = rl_grid<kRL ? B : 1>(v.n);
-    k_rl_cheb<T, TD, B, 0><<<g, RL_NT, 0, s>>>(v.rl, v.rl_dinv, v.rhs, nullptr, xo, v.d, T(0), v.c2[0], st_);
+    const int64_t g = rl_grid<kRowLanes ? B : 1>(v.n);
+    if (fused_restrict(l))
+      k_rl_cheb_restricted<T, TD, B><<<g, RL_NT, 0, s>>>(v.rl, v.rl_dinv, v.child_ptr, lev_[l - 1].S, v.rhs, xo,
+                                                          v.d, v.c2[0], st_);
+    else
+      k_rl_cheb<T, TD, B, 0><<<g, RL_NT, 0, s>>>(v.rl, v.rl_dinv, v.rhs, nullptr, xo, v.d, T(0), v.c2[0], st_);
     for (int k = 1; k < degree_; ++k) {
       k_rl_cheb<T, TD, B, 2><<<g, RL_NT, 0, s>>>(v.rl, v.rl_dinv, v.rhs, xo, xn, v.d, v.c1[k], v.c2[k], st_);
       std::swap(xo, xn);
     }
     Lev& c = lev_[l + 1];
     k_rl_resid_restrict<T, B><<<g, RL_NT, 0, s>>>(v.rl, v.rl_P, v.rhs, xo, v.S, st_);
-    k_segsum<T, B><<<cdiv(c.n * B, 256), 256, 0, s>>>(c.child_ptr, v.S, c.rhs, c.n, st_);
+    if (!fused_restrict(l + 1))
+      k_segsum<T, B><<<cdiv(c.n * B, 256), 256, 0, s>>>(c.child_ptr, v.S, c.rhs, c.n, st_);
     T* ec = vc(l + 1, s);
     k_rl_prolong<T, B><<<g, RL_NT, 0, s>>>(v.rl_P, v.parent, ec, xo, v.n, st_);
     k_rl_cheb<T, TD, B, 1><<<g, RL_NT, 0, s>>>(v.rl, v.rl_dinv, v.rhs, xo, xn, v.d, T(0), v.c2[0], st_);
@@ -568,7 +592,8 @@ class Engine : public EngineBase {
     }
     Lev& c = lev_[l + 1];
     k_resid_restrict<T, B, Op><<<g, NTB, 0, s>>>(op, v.P, v.rhs, xo, v.S, st_);
-    k_segsum<T, B><<<cdiv(c.n * B, 256), 256, 0, s>>>(c.child_ptr, v.S, c.rhs, c.n, st_);
+    if (!fused_restrict(l + 1))
+      k_segsum<T, B><<<cdiv(c.n * B, 256), 256, 0, s>>>(c.child_ptr, v.S, c.rhs, c.n, st_);
     T* ec = vc(l + 1, s);
     k_prolong<T, B, OpStreams<Op>::value><<<g, NTB, 0, s>>>(v.P, v.parent, ec, xo, v.nsl, st_);
     cheb_step<1>(op, v, xo, xn, T(0), v.c2[0], s, st_);
@@ -807,7 +832,7 @@ class Engine : public EngineBase {
         if ((rc = dalloc(&v.xb, v.nvec, err))) return rc;
         if ((rc = dalloc(&v.d, v.nvec, err))) return rc;
         if ((rc = dalloc(&v.S, v.nvec, err))) return rc;
-        if (kRL && l > 0) {
+        if (kRowLanes && l > 0) {
           std::vector<int32_t> rp(hl.A.rowptr.begin(), hl.A.rowptr.end());
           int32_t *drp, *dcol;
           T* dval;
