@@ -71,16 +71,24 @@ __device__ __forceinline__ void mf_nbr_face(const MfTablesT<R>& T, const R* xn, 
   }
 }
 
+// Minimum resident blocks of 128 threads asked of the compiler for the 2D
+// operator's kernels (AGG_MF2_MINB overrides it; 0 leaves the registers
+// free). Float32 Q2: 7 blocks (72 registers, 12 B spilled) ran the
+// Chebyshev step in 57.0 instead of 58.2 us (80 registers, 6 blocks) on the
+// 512^2 square, three runs each on one GB300; 8 blocks spilled 156 B and
+// took 85 us.
 #ifndef AGG_MF2_MINB
-#define AGG_MF2_MINB 0
+#define AGG_MF2_MINB -1
 #endif
+template <typename R, int B> struct Mf2MinBlocks { static constexpr int value = 0; };
+template <> struct Mf2MinBlocks<float, 9> { static constexpr int value = 7; };
 #ifndef AGG_MF2_DIRECT_BACK
 #define AGG_MF2_DIRECT_BACK 0
 #endif
 template <typename R, int B>
 struct MfOpV {
   static constexpr int kDegree = MfDegree<B>::value;
-  static constexpr int kMinBlocks = AGG_MF2_MINB;
+  static constexpr int kMinBlocks = (AGG_MF2_MINB >= 0) ? AGG_MF2_MINB : Mf2MinBlocks<R, B>::value;
   MfViewT<R> V;
   MfTablesT<R> T;
   __device__ __forceinline__ int64_t nslices() const { return V.nslices; }
@@ -329,6 +337,20 @@ struct MfOp3V {
 #pragma unroll
     for (int i = 0; i < B; ++i) u[i] = x[(size_t)unit * B + i];
     const R* cd = V.cell + (size_t)slice * QQ * Q * 7 * SL + lane;
+    // The test-side sums of the face terms (and for B = 64 those of the cell
+    // term too) go to the thread's column of a shared array: no register
+    // array is indexed at run time, and for B = 64 the 64 sums are not held
+    // in registers through the plane loop (254 instead of 255 registers with
+    // 136 B spilled; the 48^3 Q3 step 918 instead of 1,035 us). For B = 27
+    // the same change cut the Chebyshev step by 0.7% but slowed the time step
+    // of the 64^3 cube by 1%, so the cell sums stay in registers there.
+    // They join acc at the end.
+    constexpr bool kCellShared = (B == 64);
+    constexpr int NT = UnitThreads<B>::value;
+    __shared__ R sacc[B][NT];
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < B; ++i) sacc[i][t] = R(0);
     // ---- cell term
 #ifndef AGG_MF3_PLANE_UNROLL
 #define AGG_MF3_PLANE_UNROLL 1
@@ -413,18 +435,14 @@ struct MfOp3V {
             pw += T.L[a][k] * p2[b][k];
           }
 #pragma unroll
-          for (int c = 0; c < N; ++c) acc[a + N * b + NN * c] += Lm[c] * pv + Dm[c] * pw;
+          for (int c = 0; c < N; ++c) {
+            if constexpr (kCellShared) sacc[a + N * b + NN * c][t] += Lm[c] * pv + Dm[c] * pw;
+            else acc[a + N * b + NN * c] += Lm[c] * pv + Dm[c] * pw;
+          }
         }
     }
     // ---- face terms: one pass per face at run time; both sides' traces are
-    // read from memory through strides, the test-side sums go to the
-    // thread's column of a shared array (no register array is indexed at run
-    // time) and join acc at the end
-    constexpr int NT = UnitThreads<B>::value;
-    __shared__ R sacc[B][NT];
-    const int t = threadIdx.x;
-#pragma unroll
-    for (int i = 0; i < B; ++i) sacc[i][t] = R(0);
+    // read from memory through strides
     const R* xe = x + (size_t)unit * B;
 #pragma unroll 1
     for (int f = 0; f < 6; ++f) {
