@@ -48,7 +48,7 @@ typedef enum {
   AGG_ENOTSPD = -4,       /* a block or the coarsest matrix is not SPD         */
   AGG_ENOTCONV = -5,      /* PCG reached max_it before the tolerance           */
   AGG_ENAN = -6,          /* NaN or Inf in a residual norm                     */
-  AGG_EUNSUPPORTED = -7   /* a combination this build does not provide         */
+  AGG_EUNSUPPORTED = -7   /* a combination the library does not provide        */
 } agg_status;
 
 typedef struct agg_mesh* agg_mesh_t;
