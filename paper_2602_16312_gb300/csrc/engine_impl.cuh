@@ -50,6 +50,12 @@ template <typename T, typename TD, int B>
 class Engine : public EngineBase {
   static constexpr int NTB = UnitThreads<B>::value;
   static constexpr bool kRL = (B <= 32);
+#ifndef AGG_COARSE_NT
+#define AGG_COARSE_NT 256
+#endif
+  // threads per block of the coarsest triangular products (one warp per row;
+  // 64 measured no faster than 256)
+  static constexpr int kCoarseNT = AGG_COARSE_NT;
   // coarse levels on the row-lane kernels: warp-shuffle units (B <= 32, kRL;
   // also eligible for the persistent and cluster kernels) or shared-memory
   // units (B = 64)
@@ -353,9 +359,9 @@ class Engine : public EngineBase {
       if (cluster_ && l == lc_) return launch_cluster(s);
     }
     if (l == nlev_ - 1) {
-      const int64_t g = cdiv(nc_ * 32, 256);
-      k_coarse_lower<T><<<g, 256, 0, s>>>(Linv_, v.rhs, yc_, nc_, st_);
-      k_coarse_upper<T><<<g, 256, 0, s>>>(U_, yc_, v.xa, nc_, st_);
+      const int64_t g = cdiv(nc_ * 32, kCoarseNT);
+      k_coarse_lower<T><<<g, kCoarseNT, 0, s>>>(Linv_, v.rhs, yc_, nc_, st_);
+      k_coarse_upper<T><<<g, kCoarseNT, 0, s>>>(U_, yc_, v.xa, nc_, st_);
       return v.xa;
     }
     if constexpr (kMf) {
