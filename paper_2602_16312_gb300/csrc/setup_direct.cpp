@@ -225,7 +225,12 @@ int direct_level_build(const Mesh& m, const HostHierarchy& h, int l, double c, B
         const bool row_plus = e < n;                         // the lower element id is the + side
         face_quadrature(m, row_plus ? e : n, row_plus ? f : fn, ft, fw, fq);
         const double sgs = row_plus ? 1.0 : -1.0, sgo = -sgs;
-        const double ar = area.at({std::min(K, Kn), std::max(K, Kn)});   // read-only here
+        const auto it = area.find({std::min(K, Kn), std::max(K, Kn)});   // read-only here
+        if (it == area.end()) {                                // a face the pair scan missed
+          bad += 1;
+          continue;
+        }
+        const double ar = it->second;
         const double alpha = c_pen * std::max(ar / volK[K], ar / volK[Kn]);
         const double* Dn = &m.D[(size_t)n * dd];
         size_t slot = 0;
@@ -283,7 +288,7 @@ int direct_level_build(const Mesh& m, const HostHierarchy& h, int l, double c, B
     }
   }
   if (bad) {
-    err = "non-inherited coarse operator: non-positive Jacobian";
+    err = "non-inherited coarse operator: non-positive Jacobian or an unmatched face";
     return AGG_EINVAL;
   }
   out.nrows = nK;
